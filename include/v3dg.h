@@ -1,0 +1,187 @@
+/*
+ * v3dg.h -- C ABI of the GB300 (sm_103a) implementation of V3DG's online per-frame path:
+ * footprint-based LOD-cut selection over instanced cluster hierarchies (Sec. 3.3-3.4) followed by
+ * tile-based splatting of only the selected Gaussians (Sec. 2.1, Sec. 5.1).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a v3dg_status.  No exception or longjmp crosses this boundary.  On an
+ *    error the context keeps its previous state and v3dg_last_error() holds a one-line reason.
+ *  - "host" pointers are read during the call only; the library copies what it keeps.
+ *    "device" pointers must be CUDA device (or managed) memory of the context's device and stay
+ *    owned by the caller.
+ *  - All work is enqueued on the context's stream (v3dg_set_stream; default: the legacy stream).
+ *    Device memory the library needs comes from the allocator given to v3dg_create (e.g. a
+ *    PyTorch caching allocator) or, when none is given, from cudaMalloc.
+ *  - One context per host thread; a context is not thread-safe.
+ *  - There is no CPU fallback: without a usable CUDA device v3dg_create returns V3DG_ECUDA.
+ */
+#ifndef V3DG_H
+#define V3DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct v3dg_ctx v3dg_ctx;
+
+typedef enum {
+  V3DG_OK = 0,
+  V3DG_EINVAL = 1,     /* bad argument or malformed input; nothing changed */
+  V3DG_ENOMEM = 2,     /* allocator returned NULL; nothing changed */
+  V3DG_ECUDA = 3,      /* a CUDA call failed; the message names it */
+  V3DG_EBUSY = 4,      /* the requested result is not ready */
+  V3DG_ETIMEOUT = 5,   /* a bounded device-side wait gave up; the frame's outputs are invalid */
+  V3DG_EOVERFLOW = 6,  /* a device capacity was exceeded and could not be grown */
+  V3DG_ENOTFOUND = 7   /* unknown asset id or no frame selected yet */
+} v3dg_status;
+
+/* Device-memory provider.  alloc returns device memory of at least `bytes` bytes aligned to 256
+ * bytes, or NULL; free releases a pointer alloc returned.  `user` is passed through. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} v3dg_allocator;
+
+/* Pinhole camera V with image size w x h (Sec. 3.4 selects with "the camera view V and image
+ * resolution w x h").  OpenCV axes: x right, y down, z forward.  world_to_cam is the row-major
+ * 3x4 [R | t] mapping world points to camera space.  Intrinsics are in pixels; pixel (px, py)
+ * samples the point (px + 0.5, py + 0.5).  near_z <= 0 selects the default 0.01. */
+typedef struct {
+  double world_to_cam[12];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float near_z;
+} v3dg_camera;
+
+/* One asset's bundle (Sec. 3.1-3.2, Algorithm 1): Gaussians plus the cluster tree.
+ *  - Gaussians, SoA, host pointers, n_gauss entries each: means (3n), log_scales (3n),
+ *    quats (4n; w, x, y, z; need not be unit length), opacity (n; activated, in (0, 1]),
+ *    sh (n * (sh_degree + 1)^2 * 3; per Gaussian coefficient-major then RGB).
+ *  - Clusters (tree nodes), n_nodes entries each: node_first / node_count give the node's
+ *    Gaussians [first, first + count) with 1 <= count <= 64; node_level is 0 for the finest
+ *    clusters; node_parent is -1 for the root and otherwise a node one level up.
+ *  - own_sphere (4 * n_nodes; cx, cy, cz, r): the bounding sphere of the cluster group the node
+ *    belongs to (Sec. 3.3, Fig. 4).  The parent sphere (c_p, r_p) of Sec. 3.4 is the parent's
+ *    own sphere, so the library derives it; a leaf has F_c := 0 and the root F_p := +inf.
+ *  - gaussians_per_group: the nominal Gaussians per cluster group, used to turn a per-Gaussian
+ *    pixel tolerance into the area tolerance (tau_F = n * tau_px^2).
+ * Validation (V3DG_EINVAL): counts in range, ranges inside [0, n_gauss), parents one level up
+ * and acyclic, exactly one root, finite spheres with r >= 0, sh_degree <= 3. */
+typedef struct {
+  uint32_t n_gauss, n_nodes, sh_degree;
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity;
+  const float* sh;
+  const uint32_t* node_first;
+  const uint32_t* node_count;
+  const uint8_t* node_level;
+  const int32_t* node_parent;
+  const float* own_sphere;
+  uint32_t gaussians_per_group;
+} v3dg_hierarchy_desc;
+
+/* Counters of the last frame (filled by v3dg_frame_stats, which synchronises the stream). */
+typedef struct {
+  uint64_t cut_nodes;       /* |{(i, n) : F_c <= tau < F_p}| over all instances (Sec. 3.4) */
+  uint64_t cut_gaussians;   /* Gaussians in those clusters */
+  uint64_t render_nodes;    /* cut clusters left after the conservative visibility cull */
+  uint64_t visible;         /* Gaussians that survive the projection culls */
+  uint64_t pairs;           /* (tile, Gaussian) pairs sorted and blended */
+  uint32_t overflow;        /* nonzero if a capacity was exceeded (outputs invalid) */
+  uint32_t timeout;         /* nonzero if a bounded device wait gave up (outputs invalid) */
+} v3dg_stats;
+
+/* Options for v3dg_set_option. */
+enum {
+  V3DG_OPT_SYNC_CHECK = 1,  /* 1 (default): v3dg_render waits for the frame and re-runs it with
+                               larger buffers on overflow; 0: fully asynchronous, the caller
+                               checks v3dg_frame_stats */
+  V3DG_OPT_STAGE_TIMING = 2, /* 1: record CUDA events around every stage (see v3dg_stage_times) */
+  V3DG_OPT_CAP_NODES = 3,    /* current render-list capacity in clusters (>= 64); grows on demand */
+  V3DG_OPT_CAP_PAIRS = 4     /* current (tile, Gaussian) pair capacity (>= 4096); grows on demand */
+};
+
+/* Create a context on CUDA device `device`.  `alloc` may be NULL (cudaMalloc/cudaFree). */
+v3dg_status v3dg_create(int device, const v3dg_allocator* alloc, v3dg_ctx** out);
+/* Release every device buffer of the context (after synchronising its stream). */
+void v3dg_destroy(v3dg_ctx* ctx);
+/* Last error text of the context (never NULL; "" after success). */
+const char* v3dg_last_error(const v3dg_ctx* ctx);
+/* Stream (a cudaStream_t of the context's device) on which all later work is enqueued. */
+v3dg_status v3dg_set_stream(v3dg_ctx* ctx, void* cuda_stream);
+v3dg_status v3dg_set_option(v3dg_ctx* ctx, int option, int64_t value);
+
+/* Upload one asset's bundle (the bundles that the online stage reads, Sec. 3, Fig. 2).  The
+ * Gaussians are repacked on the device into 64-slot cluster blocks, attribute-major.  On success
+ * *asset_id receives the asset's index (0, 1, ... in load order). */
+v3dg_status v3dg_load_hierarchy(v3dg_ctx* ctx, const v3dg_hierarchy_desc* desc, uint32_t* asset_id);
+
+/* Set the composed scene (Sec. 4.2, App. B.2): n instances, instance i places asset asset_id[i]
+ * with rotation rot[9i..9i+8] (row-major, proper), translation trans[3i..3i+2] and uniform scale
+ * scale[i] > 0: x_world = scale R x_asset + t.  Host pointers, FP64.  Instances may change every
+ * frame (rigid dynamic scenes, App. B.3). */
+v3dg_status v3dg_set_instances(v3dg_ctx* ctx, uint32_t n, const uint32_t* asset_id,
+                               const double* rot, const double* trans, const double* scale);
+
+/* Select the cut for one camera (Sec. 3.4): for every instance i and cluster n, with footprints
+ * F = pi r'^2 fx fy / z^2 of the own and parent spheres (Sec. 3.3, Fig. 4; r' = s_i r, +inf when
+ * |z| <= r'), keep (i, n) iff F_c <= tau_F < F_p, with tau_F = float32(gaussians_per_group *
+ * tau_px^2).  Clusters whose Gaussians provably cannot reach a pixel are dropped afterwards (this
+ * changes no pixel).  Enqueued only; counters are available through v3dg_frame_stats. */
+v3dg_status v3dg_select(v3dg_ctx* ctx, const v3dg_camera* cam, float tau_px);
+
+/* Splat the selected Gaussians (Sec. 2.1; Sec. 5.1: no 2D dilation): projection to 2D means and
+ * conics, binning to 16x16 tiles, (tile, depth) sort with ties broken by Gaussian id, and per
+ * pixel front-to-back blending C = sum_i c_i a_i prod_{j<i}(1 - a_j) with
+ * a = min(0.999, o exp(-q/2)), a < 1/255 skipped, stopping before T < 1e-4; background 0.
+ * rgb_out: device, height * width * 3 float32 (row-major, RGB interleaved); T_out: device,
+ * height * width float32 final transmittance, or NULL.  Requires a prior v3dg_select
+ * (V3DG_ENOTFOUND otherwise). */
+v3dg_status v3dg_render(v3dg_ctx* ctx, float* rgb_out, float* T_out);
+
+/* v3dg_render into HOST buffers (same layouts): the image is produced on the device and copied
+ * back before the call returns. */
+v3dg_status v3dg_render_host(v3dg_ctx* ctx, float* rgb_host, float* T_host);
+
+/* Synchronise the stream and report the last frame's counters. */
+v3dg_status v3dg_frame_stats(v3dg_ctx* ctx, v3dg_stats* out);
+
+/* Parity read-back (synchronising, host outputs).
+ * v3dg_get_cut: the cut of the last v3dg_select before the visibility cull, as (instance, node)
+ *   pairs in ascending (instance, node) order; 2 * cap uint32 slots; *n receives the size.
+ * v3dg_get_projected: every visible Gaussian of the last render in global-id order; per entry
+ *   inst, local (asset-local Gaussian index), u (2), conic (3; q = A dx^2 + 2B dx dy + C dy^2),
+ *   opacity, rgb (3), depth_key (bits of the float32 view depth), rect (4; tx0, tx1, ty0, ty1).
+ *   Any output pointer may be NULL.
+ * v3dg_get_pairs: the sorted (tile, Gaussian) pairs of the last render, as tile id, depth key,
+ *   instance and asset-local index.
+ * v3dg_get_tile_ranges: for each tile t, [range[2t], range[2t+1]) indexes the sorted pairs. */
+v3dg_status v3dg_get_cut(v3dg_ctx* ctx, uint32_t* inst_node, uint64_t cap, uint64_t* n);
+v3dg_status v3dg_get_projected(v3dg_ctx* ctx, uint64_t cap, uint64_t* n, uint32_t* inst,
+                               uint32_t* local, float* u, float* conic, float* opacity,
+                               float* rgb, uint32_t* depth_key, int32_t* rect);
+v3dg_status v3dg_get_pairs(v3dg_ctx* ctx, uint64_t cap, uint64_t* n, uint32_t* tile,
+                           uint32_t* depth_key, uint32_t* inst, uint32_t* local);
+v3dg_status v3dg_get_tile_ranges(v3dg_ctx* ctx, uint32_t* range, uint64_t cap, uint64_t* n_tiles);
+
+/* Per-stage device times (ms) of the last frame when V3DG_OPT_STAGE_TIMING is on, in the order
+ * select, project, depth-sort, bin, tile-sort, ranges, blend; also the number of kernels the
+ * library has launched since the context was created (*launches may be NULL). */
+v3dg_status v3dg_stage_times(v3dg_ctx* ctx, float* ms, int n, uint64_t* launches);
+
+/* Stable LSD radix sort of n (key, value) uint32 pairs on key bits [begin_bit, end_bit), in
+ * place, on the context's stream (the sort of the splatting stage, exposed on its own).  keys
+ * and vals are device pointers; scratch memory comes from the context's allocator. */
+v3dg_status v3dg_sort_pairs(v3dg_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t n,
+                            int begin_bit, int end_bit);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* V3DG_H */

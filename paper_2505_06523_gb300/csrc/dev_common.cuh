@@ -1,0 +1,95 @@
+// Device helpers shared by the kernels: acquire/release accesses and the bounded chained scan.
+#pragma once
+
+#include <cstdint>
+
+#include "v3dg_internal.h"
+
+namespace v3dg {
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t pack_status(uint32_t epoch, uint64_t flag, uint32_t value) {
+  return (uint64_t(epoch) << 34) | (flag << 32) | uint64_t(value);
+}
+
+// Exclusive prefix of `agg` over all tiles before `tile` (decoupled look-back).  Tile t owns the
+// status word status[t * stride]; a word whose epoch differs from `epoch` counts as not yet
+// written, so the array never needs clearing between launches.  Called by one thread per chain.
+// Every wait is bounded: after kSpinLimit polls the thread sets *err, publishes what it has (so
+// that later tiles do not wait in turn) and returns.
+__device__ __forceinline__ uint32_t chained_exclusive(uint64_t* status, uint32_t stride, uint32_t tile,
+                                                      uint32_t agg, uint32_t epoch, uint32_t* err) {
+  if (tile == 0) {
+    st_release(status, pack_status(epoch, kFlagPrefix, agg));
+    return 0;
+  }
+  st_release(status + size_t(tile) * stride, pack_status(epoch, kFlagAgg, agg));
+  uint32_t excl = 0;
+  int64_t j = int64_t(tile) - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    const uint64_t s = ld_acquire(status + size_t(j) * stride);
+    const uint32_t flag = uint32_t(s >> 32) & 3u;
+    if (uint32_t(s >> 34) != epoch || flag == 0) {
+      if (++spins > kSpinLimit) {
+        atomicOr(err, 1u);
+        break;
+      }
+      if (spins > 32) __nanosleep(32);
+      continue;
+    }
+    excl += uint32_t(s);
+    if (flag == kFlagPrefix) break;
+    --j;
+  }
+  st_release(status + size_t(tile) * stride, pack_status(epoch, kFlagPrefix, excl + agg));
+  return excl;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Block-wide exclusive scan of one uint32 per thread (blockDim.x == 32 * NW); returns the
+// exclusive prefix and writes the block total to *total.  `scratch` holds NW + 1 words.
+template <int NW>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* scratch, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < NW ? scratch[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += t;
+    }
+    if (lane < NW) scratch[lane] = wi - w;
+    if (lane == NW - 1) scratch[NW] = wi;
+  }
+  __syncthreads();
+  const uint32_t r = scratch[warp] + incl - v;
+  *total = scratch[NW];
+  __syncthreads();
+  return r;
+}
+
+}  // namespace v3dg

@@ -1,0 +1,169 @@
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs, onesweep style.
+//
+// One histogram kernel reads the keys once and counts all digit passes; then each 8-bit pass is
+// a single kernel: a block takes the next 4096-key tile (virtual id from an atomic counter),
+// ranks its keys per digit with warp match/popc (stable: item-major then lane order within a
+// warp, warps in order), publishes its per-digit counts, and looks back across earlier tiles
+// per digit (256 threads, one chain each, bounded waits) to find its global offsets.  The tile is
+// reordered by digit in shared memory first so that the global writes come out in runs.
+#include "dev_common.cuh"
+
+namespace v3dg {
+namespace {
+
+constexpr int kBins = 256;
+constexpr int kWarps = kSortThreads / 32;
+
+__global__ void __launch_bounds__(256)
+k_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev, uint32_t cap, int begin_bit,
+       int end_bit, int passes, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[4][kBins];
+  for (int i = threadIdx.x; i < 4 * kBins; i += blockDim.x) sh[i / kBins][i % kBins] = 0;
+  __syncthreads();
+  const uint32_t n = min(*n_dev, cap);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t k = keys[i];
+    for (int p = 0; p < passes; ++p) {
+      const int sh_ = begin_bit + 8 * p;
+      const uint32_t m = end_bit - sh_ >= 8 ? 0xFFu : ((1u << (end_bit - sh_)) - 1u);
+      atomicAdd(&sh[p][(k >> sh_) & m], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kBins; i += blockDim.x) {
+    const uint32_t c = sh[i / kBins][i % kBins];
+    if (c) atomicAdd(hist + i, c);
+  }
+}
+
+template <bool kImplicit>
+__global__ void __launch_bounds__(kSortThreads)
+k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+           uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev, uint32_t cap, int shift, uint32_t dmask,
+           const uint32_t* __restrict__ ghist, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
+           uint32_t epoch, uint32_t* __restrict__ err) {
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_wh[kWarps][kBins];   // per-warp digit counts, then per-warp exclusive offsets
+  __shared__ uint32_t s_start[kBins];        // block-local start of each digit
+  __shared__ int32_t s_goff[kBins];          // global destination offset minus local start
+  __shared__ uint32_t s_scan[kWarps + 1];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+  for (int i = tid; i < kWarps * kBins; i += kSortThreads) (&s_wh[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t n = min(*n_dev, cap);
+  const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const uint32_t tile = s_tile;
+  if (tile >= ntiles) return;
+  const uint32_t base = tile * kSortTile + warp * (kSortItems * 32);
+
+  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t idx = base + i * 32 + lane;
+    const bool ok = idx < n;
+    key[i] = ok ? kin[idx] : 0xFFFFFFFFu;
+    val[i] = kImplicit ? idx : (ok ? vin[idx] : 0u);
+  }
+  // warp-level stable ranking
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t idx = base + i * 32 + lane;
+    const bool ok = idx < n;
+    const uint32_t live = __ballot_sync(0xffffffffu, ok);
+    rank[i] = 0;
+    if (ok) {
+      const uint32_t d = (key[i] >> shift) & dmask;
+      const uint32_t peers = __match_any_sync(live, d);
+      const uint32_t before = __popc(peers & lanemask_lt());
+      const uint32_t cur = s_wh[warp][d];
+      __syncwarp(live);
+      if (before == 0) s_wh[warp][d] = cur + __popc(peers);
+      __syncwarp(live);
+      rank[i] = cur + before;
+    }
+  }
+  __syncthreads();
+  // per digit: exclusive offsets across warps and the block count
+  const uint32_t d = tid;  // kSortThreads == kBins
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const uint32_t c = s_wh[w][d];
+    s_wh[w][d] = cnt;
+    cnt += c;
+  }
+  uint32_t total;
+  const uint32_t start = block_exclusive_scan<kWarps>(cnt, s_scan, &total);
+  const uint32_t gstart = block_exclusive_scan<kWarps>(ghist[d], s_scan, &total);
+  s_start[d] = start;
+  const uint32_t excl = chained_exclusive(status + d, kBins, tile, cnt, epoch, err);
+  s_goff[d] = int32_t(gstart + excl) - int32_t(start);
+  __syncthreads();
+  // reorder the tile by digit in shared memory
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t idx = base + i * 32 + lane;
+    if (idx < n) {
+      const uint32_t dg = (key[i] >> shift) & dmask;
+      const uint32_t pos = s_start[dg] + s_wh[warp][dg] + rank[i];
+      s_keys[pos] = key[i];
+      s_vals[pos] = val[i];
+    }
+  }
+  __syncthreads();
+  const uint32_t valid = min(uint32_t(kSortTile), n - tile * kSortTile);
+#pragma unroll 4
+  for (uint32_t p = tid; p < valid; p += kSortThreads) {
+    const uint32_t k = s_keys[p];
+    const uint32_t dst = uint32_t(s_goff[(k >> shift) & dmask] + int32_t(p));
+    kout[dst] = k;
+    vout[dst] = s_vals[p];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
+                        uint32_t cap, int begin_bit, int end_bit, bool implicit_vals, const SortScratch& sc,
+                        uint32_t* err_flag, uint32_t& epoch, int sm_count, cudaStream_t st, bool* result_in_1,
+                        int* launches) {
+  const int passes = (end_bit - begin_bit + 7) / 8;
+  *result_in_1 = false;
+  if (passes <= 0 || cap == 0) return cudaSuccess;
+  if (passes > 4) return cudaErrorInvalidValue;
+  const uint32_t max_tiles = (cap + kSortTile - 1) / kSortTile;
+  if (max_tiles > sc.max_tiles) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * kBins * passes, st);
+  if (e != cudaSuccess) return e;
+  k_hist<<<sm_count * 4, 256, 0, st>>>(k0, n_dev, cap, begin_bit, end_bit, passes, sc.hist);
+  ++*launches;
+  uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = begin_bit + 8 * p;
+    const uint32_t dmask = end_bit - shift >= 8 ? 0xFFu : ((1u << (end_bit - shift)) - 1u);
+    epoch = (epoch + 1) & 0x3FFFFFFFu;
+    if (epoch == 0) epoch = 1;
+    const uint32_t ep = epoch;
+    if (p == 0 && implicit_vals)
+      k_onesweep<true><<<max_tiles, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + kBins * p,
+                                                           sc.status, sc.tile_counters + p, ep, err_flag);
+    else
+      k_onesweep<false><<<max_tiles, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + kBins * p,
+                                                            sc.status, sc.tile_counters + p, ep, err_flag);
+    ++*launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uint32_t* t;
+    t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+  }
+  *result_in_1 = (passes & 1) != 0;
+  return cudaSuccess;
+}
+
+}  // namespace v3dg

@@ -1,0 +1,904 @@
+// Host side of the C ABI declared in include/v3dg.h.
+//
+// Owns the device state of one context: the uploaded bundles (Sec. 3, Fig. 2), the instance table
+// (Sec. 4.2), the per-frame FP64 set-up (camera V and instances composed into M = W [s R | t])
+// and the work buffers of the splatting stages, whose capacities grow when a frame overflows.
+// Host code is compiled with -ffp-contract=off: M is composed in a fixed operation order.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "v3dg.h"
+#include "v3dg_internal.h"
+
+using namespace v3dg;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct AssetHost {
+  uint32_t n_gauss = 0, n_nodes = 0, sh_coeffs = 0, gpg = 0;
+  std::vector<uint32_t> node_first;
+  DevBuf own, par, bound, sigma, flags, cnt, attr;
+};
+
+constexpr uint32_t kInitNodes = 1u << 14;
+constexpr uint32_t kInitPairs = 1u << 22;
+constexpr uint32_t kMaxNodes = 1u << 24;
+constexpr uint32_t kMaxPairs = (1u << 31) - 1u;
+enum { kStageSelect = 0, kStageProject, kStageDepthSort, kStageBin, kStageTileSort, kStageRanges, kStageBlend, kStages };
+
+}  // namespace
+
+struct v3dg_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  v3dg_allocator alloc{};
+  bool has_alloc = false;
+  std::string err;
+
+  std::vector<AssetHost> assets;
+  DevBuf d_assets;
+
+  std::vector<uint32_t> inst_asset;
+  std::vector<double> inst_rot, inst_trans, inst_scale;
+
+  bool selected = false, rendered = false;
+  v3dg_camera cam{};
+  float tau_px = 0.f;
+  CamConst cc{};
+  uint32_t n_inst_frame = 0;
+  int node_blocks = 0;
+
+  DevBuf d_inst;
+  InstFrame* h_inst = nullptr;
+  size_t h_inst_cap = 0;
+  cudaEvent_t ev_inst = nullptr;
+  DevBuf d_frame, d_cutframe, d_misc;
+  uint32_t* h_frame = nullptr;   // pinned copy of the frame words, written at the end of each frame
+  uint32_t* h_tmp = nullptr;     // pinned scratch words
+
+  uint32_t cap_nodes = 0, cap_slots = 0, cap_pairs = 0, status_words = 0, cap_cut = 0;
+  DevBuf d_list, d_ref, d_keys0, d_keys1, d_vals0, d_vals1, d_rec, d_rect, d_off;
+  DevBuf d_pk0, d_pk1, d_pv0, d_pv1, d_ranges, d_status, d_hist, d_cut;
+  DevBuf d_img, d_timg, d_sort_k, d_sort_v;
+  bool depth_in1 = false, tiles_in1 = false;
+  uint32_t epoch = 1;
+  uint64_t launches = 0;
+  bool sync_check = true, stage_timing = false;
+  cudaEvent_t ev[kStages + 1] = {};
+};
+
+namespace {
+
+v3dg_status fail(v3dg_ctx* c, v3dg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(c, V3DG_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+#define ST(call)                                                                                   \
+  do {                                                                                             \
+    v3dg_status s_ = (call);                                                                       \
+    if (s_ != V3DG_OK) return s_;                                                                  \
+  } while (0)
+
+void dfree(v3dg_ctx* c, DevBuf& b) {
+  if (b.p) {
+    if (c->has_alloc)
+      c->alloc.free(b.p, c->alloc.user);
+    else
+      cudaFree(b.p);
+  }
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+v3dg_status dalloc(v3dg_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (c->has_alloc) {
+    p = c->alloc.alloc(bytes, c->alloc.user);
+    if (!p) return fail(c, V3DG_ENOMEM, "allocator returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, V3DG_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  dfree(c, b);
+  b.p = p;
+  b.bytes = bytes;
+  if (zero) CU(cudaMemsetAsync(p, 0, bytes, c->stream));
+  return V3DG_OK;
+}
+
+v3dg_status ensure(v3dg_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
+  if (b.p && b.bytes >= bytes) return V3DG_OK;
+  return dalloc(c, b, bytes, zero);
+}
+
+template <class T>
+T* P(const DevBuf& b) {
+  return static_cast<T*>(b.p);
+}
+
+uint32_t next_epoch(v3dg_ctx* c) {
+  c->epoch = (c->epoch + 1) & 0x3FFFFFFFu;
+  if (c->epoch == 0) c->epoch = 1;
+  return c->epoch;
+}
+
+float round_up_f(double x) {
+  float f = float(x);
+  if (double(f) < x) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+v3dg_status ensure_status(v3dg_ctx* c, uint64_t words) {
+  if (words <= c->status_words && c->d_status.p) return V3DG_OK;
+  if (words > 0xFFFFFFFFull) return fail(c, V3DG_EOVERFLOW, "status array too large");
+  ST(dalloc(c, c->d_status, 8 * words, true));
+  c->status_words = uint32_t(words);
+  return V3DG_OK;
+}
+
+// Work buffers sized by the current capacities.
+v3dg_status ensure_work(v3dg_ctx* c) {
+  if (c->cap_nodes == 0) c->cap_nodes = kInitNodes;
+  if (c->cap_pairs == 0) c->cap_pairs = kInitPairs;
+  c->cap_slots = c->cap_nodes * uint32_t(kSlots);
+  const size_t S = c->cap_slots, PP = c->cap_pairs;
+  ST(ensure(c, c->d_list, sizeof(uint2) * c->cap_nodes));
+  ST(ensure(c, c->d_ref, sizeof(float4) * 2 * c->cap_nodes));
+  ST(ensure(c, c->d_keys0, 4 * S));
+  ST(ensure(c, c->d_keys1, 4 * S));
+  ST(ensure(c, c->d_vals0, 4 * S));
+  ST(ensure(c, c->d_vals1, 4 * S));
+  ST(ensure(c, c->d_rec, sizeof(float4) * 3 * S));
+  ST(ensure(c, c->d_rect, sizeof(uint2) * S));
+  ST(ensure(c, c->d_off, 4 * S));
+  ST(ensure(c, c->d_pk0, 4 * PP));
+  ST(ensure(c, c->d_pk1, 4 * PP));
+  ST(ensure(c, c->d_pv0, 4 * PP));
+  ST(ensure(c, c->d_pv1, 4 * PP));
+  const uint64_t sort_tiles = (std::max<uint64_t>(S, PP) + kSortTile - 1) / kSortTile;
+  uint64_t words = sort_tiles * 256;
+  words = std::max<uint64_t>(words, uint64_t(c->n_inst_frame) * uint64_t(std::max(c->node_blocks, 1)));
+  words = std::max<uint64_t>(words, (uint64_t(S) + 1023) / 1024);
+  ST(ensure_status(c, words));
+  ST(ensure(c, c->d_hist, 4 * 256 * 4));
+  return V3DG_OK;
+}
+
+SortScratch sort_scratch(v3dg_ctx* c, uint32_t* tile_counters) {
+  SortScratch sc;
+  sc.hist = P<uint32_t>(c->d_hist);
+  sc.status = P<uint64_t>(c->d_status);
+  sc.max_tiles = c->status_words / 256;
+  sc.tile_counters = tile_counters;
+  return sc;
+}
+
+void stage_event(v3dg_ctx* c, int i) {
+  if (c->stage_timing) cudaEventRecord(c->ev[i], c->stream);
+}
+
+// ------------------------------------------------------------------ per-frame set-up (FP64, host)
+
+v3dg_status setup_frame(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
+  if (!cam) return fail(c, V3DG_EINVAL, "camera is NULL");
+  if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 * 16 || cam->height > 65535 * 16)
+    return fail(c, V3DG_EINVAL, "bad image size %d x %d", cam->width, cam->height);
+  if (!(cam->fx > 0.f) || !(cam->fy > 0.f) || !std::isfinite(cam->fx) || !std::isfinite(cam->fy) ||
+      !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
+    return fail(c, V3DG_EINVAL, "bad intrinsics");
+  for (double v : cam->world_to_cam)
+    if (!std::isfinite(v)) return fail(c, V3DG_EINVAL, "non-finite world_to_cam");
+  if (!(tau_px >= 0.f) || !std::isfinite(tau_px)) return fail(c, V3DG_EINVAL, "tau_px must be finite and >= 0");
+  if (c->assets.empty()) return fail(c, V3DG_ENOTFOUND, "no hierarchy loaded");
+  const uint64_t tiles = uint64_t((cam->width + kTile - 1) / kTile) * uint64_t((cam->height + kTile - 1) / kTile);
+  if (tiles > (1u << 24)) return fail(c, V3DG_EINVAL, "image too large (%llu tiles)", (unsigned long long)tiles);
+  const uint32_t n = uint32_t(c->inst_asset.size());
+
+  c->cam = *cam;
+  if (!(c->cam.near_z > 0.f)) c->cam.near_z = 0.01f;
+  c->tau_px = tau_px;
+  CamConst& k = c->cc;
+  k.fx = cam->fx; k.fy = cam->fy; k.cx = cam->cx; k.cy = cam->cy;
+  k.near_z = c->cam.near_z;
+  k.width = cam->width; k.height = cam->height;
+  k.tiles_x = (cam->width + kTile - 1) / kTile;
+  k.tiles_y = (cam->height + kTile - 1) / kTile;
+  k.limx = 1.3f * (0.5f * float(cam->width) / cam->fx);
+  k.limy = 1.3f * (0.5f * float(cam->height) / cam->fy);
+  k.k_foot = M_PI * double(cam->fx) * double(cam->fy);
+  k.k_foot32 = float(k.k_foot);
+  const double two_ln255 = 2.0 * std::log(255.0);
+  k.cull_kx = float(std::sqrt(two_ln255 * (1.0 + double(k.limx) * double(k.limx))) * 1.01);
+  k.cull_ky = float(std::sqrt(two_ln255 * (1.0 + double(k.limy) * double(k.limy))) * 1.01);
+
+  uint32_t max_nodes = 0;
+  for (auto& a : c->assets) max_nodes = std::max(max_nodes, a.n_nodes);
+  c->node_blocks = int((max_nodes + 255) / 256);
+  c->n_inst_frame = n;
+
+  // the pinned staging buffer is reused: wait until the previous upload out of it has completed
+  if (c->ev_inst) CU(cudaEventSynchronize(c->ev_inst));
+  if (c->h_inst_cap < std::max<uint32_t>(n, 1)) {
+    if (c->h_inst) cudaFreeHost(c->h_inst);
+    c->h_inst = nullptr;
+    c->h_inst_cap = 0;
+    CU(cudaMallocHost(&c->h_inst, sizeof(InstFrame) * std::max<uint32_t>(n, 1)));
+    c->h_inst_cap = std::max<uint32_t>(n, 1);
+  }
+  ST(ensure(c, c->d_inst, sizeof(InstFrame) * std::max<uint32_t>(n, 1)));
+
+  const double* W = cam->world_to_cam;
+  double C[3];  // camera centre -R_w^T t_w
+  for (int j = 0; j < 3; ++j) C[j] = -((W[0 * 4 + j] * W[3] + W[1 * 4 + j] * W[7]) + W[2 * 4 + j] * W[11]);
+  for (uint32_t i = 0; i < n; ++i) {
+    InstFrame& f = c->h_inst[i];
+    std::memset(&f, 0, sizeof f);
+    const double* R = &c->inst_rot[9 * size_t(i)];
+    const double* t = &c->inst_trans[3 * size_t(i)];
+    const double s = c->inst_scale[i];
+    double A[9];
+    for (int q = 0; q < 9; ++q) A[q] = s * R[q];
+    for (int r = 0; r < 3; ++r) {
+      for (int col = 0; col < 3; ++col)
+        f.m64[4 * r + col] = (W[4 * r + 0] * A[0 * 3 + col] + W[4 * r + 1] * A[1 * 3 + col]) + W[4 * r + 2] * A[2 * 3 + col];
+      f.m64[4 * r + 3] = ((W[4 * r + 0] * t[0] + W[4 * r + 1] * t[1]) + W[4 * r + 2] * t[2]) + W[4 * r + 3];
+    }
+    for (int q = 0; q < 12; ++q) f.m[q] = float(f.m64[q]);
+    for (int j = 0; j < 3; ++j) {
+      const double d = (R[0 * 3 + j] * (C[0] - t[0]) + R[1 * 3 + j] * (C[1] - t[1])) + R[2 * 3 + j] * (C[2] - t[2]);
+      f.cam_a[j] = float(d / s);
+    }
+    f.s = float(s);
+    f.s64 = s;
+    const uint32_t a = c->inst_asset[i];
+    f.asset = a;
+    f.tau_f = float(double(c->assets[a].gpg) * double(tau_px) * double(tau_px));
+  }
+  if (n) CU(cudaMemcpyAsync(c->d_inst.p, c->h_inst, sizeof(InstFrame) * n, cudaMemcpyHostToDevice, c->stream));
+  if (!c->ev_inst) CU(cudaEventCreateWithFlags(&c->ev_inst, cudaEventDisableTiming));
+  CU(cudaEventRecord(c->ev_inst, c->stream));
+  return V3DG_OK;
+}
+
+v3dg_status enqueue_select(v3dg_ctx* c) {
+  ST(ensure_work(c));
+  CU(cudaMemsetAsync(c->d_frame.p, 0, sizeof(uint32_t) * kFrameWords, c->stream));
+  stage_event(c, kStageSelect);
+  if (c->n_inst_frame) {
+    CU(launch_select(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->d_assets), c->node_blocks, c->cc, 0,
+                     P<uint2>(c->d_list), c->cap_nodes, P<uint32_t>(c->d_frame), 0, P<uint64_t>(c->d_status),
+                     next_epoch(c), c->stream));
+    ++c->launches;
+  }
+  return V3DG_OK;
+}
+
+__global__ void k_slot_count(uint32_t* frame, uint32_t cap_nodes) {
+  frame[kSlotCount] = min(frame[kRenderNodes], cap_nodes) * uint32_t(kSlots);
+}
+
+__global__ void k_set_word(uint32_t* p, uint32_t v) { *p = v; }
+
+v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
+  const CamConst& k = c->cc;
+  uint32_t* frame = P<uint32_t>(c->d_frame);
+  const int sm = c->sm_count;
+  stage_event(c, kStageProject);
+  k_slot_count<<<1, 1, 0, c->stream>>>(frame, c->cap_nodes);
+  CU(cudaGetLastError());
+  CU(launch_noderef(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->d_assets), k,
+                    P<float4>(c->d_ref), frame, sm, c->stream));
+  CU(launch_project(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->d_assets), k,
+                    P<float4>(c->d_ref), P<float4>(c->d_rec), P<uint2>(c->d_rect), P<uint32_t>(c->d_keys0), frame, sm,
+                    c->stream));
+  c->launches += 3;
+
+  stage_event(c, kStageDepthSort);
+  bool in1 = false;
+  int nl = 0;
+  CU(launch_sort(P<uint32_t>(c->d_keys0), P<uint32_t>(c->d_vals0), P<uint32_t>(c->d_keys1), P<uint32_t>(c->d_vals1),
+                 frame + kSlotCount, c->cap_slots, 0, 32, true, sort_scratch(c, frame + kTileCounters + 2),
+                 frame + kTimeout, c->epoch, sm, c->stream, &in1, &nl));
+  next_epoch(c);
+  c->launches += nl;
+  c->depth_in1 = in1;
+  const uint32_t* dslots = in1 ? P<uint32_t>(c->d_vals1) : P<uint32_t>(c->d_vals0);
+
+  stage_event(c, kStageBin);
+  CU(launch_pair_scan(dslots, P<uint2>(c->d_rect), c->cap_slots, P<uint32_t>(c->d_off), frame, 1,
+                      P<uint64_t>(c->d_status), next_epoch(c), c->stream));
+  CU(launch_duplicate(dslots, P<uint2>(c->d_rect), P<uint32_t>(c->d_off), c->cap_slots, c->cap_pairs, k.tiles_x,
+                      P<uint32_t>(c->d_pk0), P<uint32_t>(c->d_pv0), frame, sm, c->stream));
+  c->launches += 3;
+
+  stage_event(c, kStageTileSort);
+  const int n_tiles = k.tiles_x * k.tiles_y;
+  int tile_bits = 1;
+  while ((1 << tile_bits) < n_tiles) ++tile_bits;
+  bool tin1 = false;
+  nl = 0;
+  CU(launch_sort(P<uint32_t>(c->d_pk0), P<uint32_t>(c->d_pv0), P<uint32_t>(c->d_pk1), P<uint32_t>(c->d_pv1),
+                 frame + kPairsEff, c->cap_pairs, 0, tile_bits, false, sort_scratch(c, frame + kTileCounters + 6),
+                 frame + kTimeout, c->epoch, sm, c->stream, &tin1, &nl));
+  next_epoch(c);
+  c->launches += nl;
+  c->tiles_in1 = tin1;
+  const uint32_t* tk = tin1 ? P<uint32_t>(c->d_pk1) : P<uint32_t>(c->d_pk0);
+  const uint32_t* tv = tin1 ? P<uint32_t>(c->d_pv1) : P<uint32_t>(c->d_pv0);
+
+  stage_event(c, kStageRanges);
+  ST(ensure(c, c->d_ranges, sizeof(uint2) * size_t(n_tiles)));
+  CU(launch_ranges(tk, c->cap_pairs, frame, P<uint2>(c->d_ranges), n_tiles, sm, c->stream));
+  c->launches += 1;
+
+  stage_event(c, kStageBlend);
+  CU(launch_blend(P<uint2>(c->d_ranges), tv, P<float4>(c->d_rec), c->cap_slots, k, rgb, t_out, c->stream));
+  c->launches += 1;
+  stage_event(c, kStages);
+  CU(cudaMemcpyAsync(c->h_frame, c->d_frame.p, sizeof(uint32_t) * kFrameWords, cudaMemcpyDeviceToHost, c->stream));
+  c->rendered = true;
+  return V3DG_OK;
+}
+
+// Runs the frame; with sync checking, waits and re-runs it with larger buffers on overflow.
+v3dg_status run_frame(v3dg_ctx* c, float* rgb, float* t_out) {
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    ST(enqueue_render(c, rgb, t_out));
+    if (!c->sync_check) return V3DG_OK;
+    CU(cudaStreamSynchronize(c->stream));
+    const uint32_t* f = c->h_frame;
+    if (f[kTimeout]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up; frame invalid");
+    if (!f[kOverflow]) return V3DG_OK;
+    bool grew = false;
+    if (f[kRenderNodes] > c->cap_nodes) {
+      const uint64_t want = uint64_t(f[kRenderNodes]) * 5 / 4 + 1024;
+      if (want > kMaxNodes) return fail(c, V3DG_EOVERFLOW, "render list of %u nodes exceeds the limit", f[kRenderNodes]);
+      c->cap_nodes = uint32_t(want);
+      grew = true;
+    }
+    if (f[kPairs] >= c->cap_pairs || !grew) {
+      const uint64_t want = std::max<uint64_t>(uint64_t(f[kPairs]) * 5 / 4, uint64_t(c->cap_pairs) * 2);
+      if (want > kMaxPairs) return fail(c, V3DG_EOVERFLOW, "%u pairs exceed the limit", f[kPairs]);
+      c->cap_pairs = uint32_t(want);
+    }
+    ST(enqueue_select(c));
+  }
+  return fail(c, V3DG_EOVERFLOW, "frame still overflows after growing the buffers");
+}
+
+v3dg_status sync_frame(v3dg_ctx* c) {
+  CU(cudaStreamSynchronize(c->stream));
+  if (!c->rendered) CU(cudaMemcpy(c->h_frame, c->d_frame.p, sizeof(uint32_t) * kFrameWords, cudaMemcpyDeviceToHost));
+  return V3DG_OK;
+}
+
+// The cut itself (mode 1), into d_cut; returns its size.
+v3dg_status run_cut(v3dg_ctx* c, uint32_t* n_cut, uint32_t* n_gauss) {
+  if (!c->selected) return fail(c, V3DG_ENOTFOUND, "no frame selected");
+  if (c->cap_cut == 0) c->cap_cut = 1u << 16;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    ST(ensure(c, c->d_cut, sizeof(uint2) * size_t(c->cap_cut)));
+    CU(cudaMemsetAsync(c->d_cutframe.p, 0, sizeof(uint32_t) * kFrameWords, c->stream));
+    if (c->n_inst_frame) {
+      CU(launch_select(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->d_assets), c->node_blocks, c->cc, 1,
+                       P<uint2>(c->d_cut), c->cap_cut, P<uint32_t>(c->d_cutframe), 0, P<uint64_t>(c->d_status),
+                       next_epoch(c), c->stream));
+      ++c->launches;
+    }
+    CU(cudaMemcpyAsync(c->h_tmp, c->d_cutframe.p, sizeof(uint32_t) * kFrameWords, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (c->h_tmp[kTimeout]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up");
+    if (!c->h_tmp[kOverflow]) {
+      *n_cut = c->h_tmp[kCutNodes];
+      *n_gauss = c->h_tmp[kCutGauss];
+      return V3DG_OK;
+    }
+    c->cap_cut = std::max(c->cap_cut * 2, c->h_tmp[kCutNodes] + 1024);
+  }
+  return fail(c, V3DG_EOVERFLOW, "cut read-back overflow");
+}
+
+v3dg_status validate_desc(v3dg_ctx* c, const v3dg_hierarchy_desc* d) {
+  if (!d) return fail(c, V3DG_EINVAL, "descriptor is NULL");
+  if (d->n_gauss == 0 || d->n_nodes == 0) return fail(c, V3DG_EINVAL, "empty hierarchy");
+  if (d->n_nodes > (1u << 24)) return fail(c, V3DG_EINVAL, "too many nodes (%u)", d->n_nodes);
+  if (d->sh_degree > 3) return fail(c, V3DG_EINVAL, "sh_degree %u > 3", d->sh_degree);
+  if (!d->means || !d->log_scales || !d->quats || !d->opacity || !d->sh || !d->node_first || !d->node_count ||
+      !d->node_level || !d->node_parent || !d->own_sphere)
+    return fail(c, V3DG_EINVAL, "NULL array in descriptor");
+  if (d->gaussians_per_group == 0) return fail(c, V3DG_EINVAL, "gaussians_per_group must be >= 1");
+  int roots = 0;
+  std::vector<uint32_t> children(d->n_nodes, 0);
+  for (uint32_t n = 0; n < d->n_nodes; ++n) {
+    const uint32_t cnt = d->node_count[n];
+    if (cnt < 1 || cnt > uint32_t(kSlots)) return fail(c, V3DG_EINVAL, "node %u has %u Gaussians (1..64)", n, cnt);
+    if (uint64_t(d->node_first[n]) + cnt > d->n_gauss) return fail(c, V3DG_EINVAL, "node %u range out of bounds", n);
+    const int32_t p = d->node_parent[n];
+    if (p < 0) {
+      ++roots;
+    } else {
+      if (uint32_t(p) >= d->n_nodes) return fail(c, V3DG_EINVAL, "node %u parent %d out of range", n, p);
+      if (d->node_level[p] != d->node_level[n] + 1) return fail(c, V3DG_EINVAL, "node %u: parent not one level up", n);
+      ++children[p];
+    }
+    const float* s = d->own_sphere + 4 * size_t(n);
+    for (int q = 0; q < 4; ++q)
+      if (!std::isfinite(s[q])) return fail(c, V3DG_EINVAL, "node %u sphere not finite", n);
+    if (s[3] < 0.f) return fail(c, V3DG_EINVAL, "node %u sphere radius < 0", n);
+  }
+  if (roots != 1) return fail(c, V3DG_EINVAL, "%d roots (need exactly 1)", roots);
+  for (uint32_t n = 0; n < d->n_nodes; ++n)
+    if (d->node_level[n] > 0 && children[n] == 0) return fail(c, V3DG_EINVAL, "interior node %u has no children", n);
+  return V3DG_OK;
+}
+
+}  // namespace
+
+// ====================================================================== public ABI
+
+extern "C" {
+
+v3dg_status v3dg_create(int device, const v3dg_allocator* alloc, v3dg_ctx** out) {
+  if (!out) return V3DG_EINVAL;
+  *out = nullptr;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || n_dev == 0) {
+    cudaGetLastError();
+    return V3DG_ECUDA;
+  }
+  if (device < 0 || device >= n_dev) return V3DG_EINVAL;
+  if (alloc && (!alloc->alloc || !alloc->free)) return V3DG_EINVAL;
+  v3dg_ctx* c = new (std::nothrow) v3dg_ctx;
+  if (!c) return V3DG_ENOMEM;
+  c->device = device;
+  if (alloc) {
+    c->alloc = *alloc;
+    c->has_alloc = true;
+  }
+  auto bail = [&](v3dg_status s) {
+    v3dg_destroy(c);
+    return s;
+  };
+  if (cudaSetDevice(device) != cudaSuccess) return bail(V3DG_ECUDA);
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return bail(V3DG_ECUDA);
+  if (cudaMallocHost(&c->h_frame, sizeof(uint32_t) * kFrameWords) != cudaSuccess) return bail(V3DG_ECUDA);
+  if (cudaMallocHost(&c->h_tmp, sizeof(uint32_t) * kFrameWords) != cudaSuccess) return bail(V3DG_ECUDA);
+  std::memset(c->h_frame, 0, sizeof(uint32_t) * kFrameWords);
+  if (dalloc(c, c->d_frame, sizeof(uint32_t) * kFrameWords, true) != V3DG_OK) return bail(V3DG_ENOMEM);
+  if (dalloc(c, c->d_cutframe, sizeof(uint32_t) * kFrameWords, true) != V3DG_OK) return bail(V3DG_ENOMEM);
+  if (dalloc(c, c->d_misc, sizeof(uint32_t) * 64, true) != V3DG_OK) return bail(V3DG_ENOMEM);
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return bail(V3DG_ECUDA);
+  *out = c;
+  return V3DG_OK;
+}
+
+void v3dg_destroy(v3dg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaDeviceSynchronize();
+  for (auto& a : c->assets) {
+    DevBuf* bs[] = {&a.own, &a.par, &a.bound, &a.sigma, &a.flags, &a.cnt, &a.attr};
+    for (DevBuf* b : bs) dfree(c, *b);
+  }
+  DevBuf* bs[] = {&c->d_assets, &c->d_inst, &c->d_frame, &c->d_cutframe, &c->d_misc, &c->d_list, &c->d_ref,
+                  &c->d_keys0, &c->d_keys1, &c->d_vals0, &c->d_vals1, &c->d_rec, &c->d_rect, &c->d_off, &c->d_pk0,
+                  &c->d_pk1, &c->d_pv0, &c->d_pv1, &c->d_ranges, &c->d_status, &c->d_hist, &c->d_cut, &c->d_img,
+                  &c->d_timg, &c->d_sort_k, &c->d_sort_v};
+  for (DevBuf* b : bs) dfree(c, *b);
+  if (c->h_inst) cudaFreeHost(c->h_inst);
+  if (c->h_frame) cudaFreeHost(c->h_frame);
+  if (c->h_tmp) cudaFreeHost(c->h_tmp);
+  if (c->ev_inst) cudaEventDestroy(c->ev_inst);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* v3dg_last_error(const v3dg_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+v3dg_status v3dg_set_stream(v3dg_ctx* c, void* stream) {
+  if (!c) return V3DG_EINVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_set_option(v3dg_ctx* c, int option, int64_t value) {
+  if (!c) return V3DG_EINVAL;
+  switch (option) {
+    case V3DG_OPT_SYNC_CHECK: c->sync_check = value != 0; break;
+    case V3DG_OPT_STAGE_TIMING: c->stage_timing = value != 0; break;
+    case V3DG_OPT_CAP_NODES:
+      if (value < 64 || value > int64_t(kMaxNodes)) return fail(c, V3DG_EINVAL, "node capacity out of range");
+      c->cap_nodes = uint32_t(value);
+      break;
+    case V3DG_OPT_CAP_PAIRS:
+      if (value < 4096 || value > int64_t(kMaxPairs)) return fail(c, V3DG_EINVAL, "pair capacity out of range");
+      c->cap_pairs = uint32_t(value);
+      break;
+    default: return fail(c, V3DG_EINVAL, "unknown option %d", option);
+  }
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint32_t* asset_id) {
+  if (!c) return V3DG_EINVAL;
+  ST(validate_desc(c, d));
+  CU(cudaSetDevice(c->device));
+  const uint32_t nn = d->n_nodes;
+  const uint32_t coeffs = (d->sh_degree + 1) * (d->sh_degree + 1);
+  const size_t stride = size_t(nn) * kSlots;
+  const int planes = attr_planes(int(coeffs));
+  std::vector<float4> own(nn), par(nn), bound(nn);
+  std::vector<float> sigma(nn);
+  std::vector<uint8_t> flags(nn), cnt(nn);
+  std::vector<float> attr(size_t(planes) * stride, 0.f);
+  for (uint32_t n = 0; n < nn; ++n) {
+    const float* s = d->own_sphere + 4 * size_t(n);
+    own[n] = make_float4(s[0], s[1], s[2], s[3]);
+  }
+  for (uint32_t n = 0; n < nn; ++n) {
+    const int32_t p = d->node_parent[n];
+    par[n] = own[p < 0 ? n : uint32_t(p)];
+    flags[n] = uint8_t((d->node_level[n] == 0 ? kLeaf : 0) | (p < 0 ? kRoot : 0));
+    const uint32_t f = d->node_first[n], k = d->node_count[n];
+    cnt[n] = uint8_t(k);
+    double mx = 0, my = 0, mz = 0, smax = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+      const float* m = d->means + 3 * size_t(f + j);
+      mx += m[0]; my += m[1]; mz += m[2];
+    }
+    const float cx = float(mx / k), cy = float(my / k), cz = float(mz / k);
+    double rho = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+      const size_t g = f + j;
+      const float* m = d->means + 3 * g;
+      const double dx = double(m[0]) - cx, dy = double(m[1]) - cy, dz = double(m[2]) - cz;
+      rho = std::max(rho, std::sqrt(dx * dx + dy * dy + dz * dz));
+      const float* ls = d->log_scales + 3 * g;
+      smax = std::max(smax, std::exp(double(std::max(ls[0], std::max(ls[1], ls[2])))));
+      const size_t slot = size_t(n) * kSlots + j;
+      attr[kX * stride + slot] = m[0];
+      attr[kY * stride + slot] = m[1];
+      attr[kZ * stride + slot] = m[2];
+      attr[kOpacity * stride + slot] = d->opacity[g];
+      for (int q = 0; q < 3; ++q) attr[(kLs0 + q) * stride + slot] = ls[q];
+      for (int q = 0; q < 4; ++q) attr[(kQw + q) * stride + slot] = d->quats[4 * g + q];
+      const float* sh = d->sh + g * coeffs * 3;
+      for (uint32_t q = 0; q < coeffs * 3; ++q) attr[(kSh0 + q) * stride + slot] = sh[q];
+    }
+    bound[n] = make_float4(cx, cy, cz, round_up_f(rho * (1.0 + 1e-6)));
+    sigma[n] = round_up_f(smax * (1.0 + 1e-6));
+    for (uint32_t j = 0; j < k; ++j) {
+      const size_t g = f + j;
+      if (!std::isfinite(d->opacity[g]) || !std::isfinite(d->means[3 * g]) || !std::isfinite(d->means[3 * g + 1]) ||
+          !std::isfinite(d->means[3 * g + 2]))
+        return fail(c, V3DG_EINVAL, "non-finite Gaussian %zu", g);
+    }
+  }
+  AssetHost a;
+  a.n_gauss = d->n_gauss;
+  a.n_nodes = nn;
+  a.sh_coeffs = coeffs;
+  a.gpg = d->gaussians_per_group;
+  a.node_first.assign(d->node_first, d->node_first + nn);
+  auto up = [&](DevBuf& b, const void* src, size_t bytes) -> v3dg_status {
+    ST(dalloc(c, b, bytes));
+    CU(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
+    return V3DG_OK;
+  };
+  v3dg_status s = V3DG_OK;
+  if ((s = up(a.own, own.data(), sizeof(float4) * nn)) != V3DG_OK || (s = up(a.par, par.data(), sizeof(float4) * nn)) != V3DG_OK ||
+      (s = up(a.bound, bound.data(), sizeof(float4) * nn)) != V3DG_OK ||
+      (s = up(a.sigma, sigma.data(), sizeof(float) * nn)) != V3DG_OK ||
+      (s = up(a.flags, flags.data(), nn)) != V3DG_OK || (s = up(a.cnt, cnt.data(), nn)) != V3DG_OK ||
+      (s = up(a.attr, attr.data(), sizeof(float) * attr.size())) != V3DG_OK) {
+    DevBuf* bs[] = {&a.own, &a.par, &a.bound, &a.sigma, &a.flags, &a.cnt, &a.attr};
+    for (DevBuf* b : bs) dfree(c, *b);
+    return s;
+  }
+  c->assets.push_back(std::move(a));
+  std::vector<AssetDev> table(c->assets.size());
+  for (size_t i = 0; i < c->assets.size(); ++i) {
+    const AssetHost& h = c->assets[i];
+    AssetDev& t = table[i];
+    t.own = P<float4>(h.own);
+    t.par = P<float4>(h.par);
+    t.bound = P<float4>(h.bound);
+    t.sigma_max = P<float>(h.sigma);
+    t.flags = P<uint8_t>(h.flags);
+    t.count = P<uint8_t>(h.cnt);
+    t.attr = P<float>(h.attr);
+    t.n_nodes = h.n_nodes;
+    t.stride = h.n_nodes * uint32_t(kSlots);
+    t.sh_coeffs = h.sh_coeffs;
+    t.pad = 0;
+  }
+  ST(ensure(c, c->d_assets, sizeof(AssetDev) * table.size()));
+  CU(cudaMemcpy(c->d_assets.p, table.data(), sizeof(AssetDev) * table.size(), cudaMemcpyHostToDevice));
+  if (asset_id) *asset_id = uint32_t(c->assets.size() - 1);
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_set_instances(v3dg_ctx* c, uint32_t n, const uint32_t* asset_id, const double* rot, const double* trans,
+                               const double* scale) {
+  if (!c) return V3DG_EINVAL;
+  if (n && (!asset_id || !rot || !trans || !scale)) return fail(c, V3DG_EINVAL, "NULL instance array");
+  for (uint32_t i = 0; i < n; ++i) {
+    if (asset_id[i] >= c->assets.size()) return fail(c, V3DG_ENOTFOUND, "instance %u: unknown asset %u", i, asset_id[i]);
+    if (!(scale[i] > 0.0) || !std::isfinite(scale[i])) return fail(c, V3DG_EINVAL, "instance %u: scale must be > 0", i);
+    for (int q = 0; q < 9; ++q)
+      if (!std::isfinite(rot[9 * size_t(i) + q])) return fail(c, V3DG_EINVAL, "instance %u: rotation not finite", i);
+    for (int q = 0; q < 3; ++q)
+      if (!std::isfinite(trans[3 * size_t(i) + q])) return fail(c, V3DG_EINVAL, "instance %u: translation not finite", i);
+  }
+  c->inst_asset.assign(asset_id, asset_id + n);
+  c->inst_rot.assign(rot, rot + 9 * size_t(n));
+  c->inst_trans.assign(trans, trans + 3 * size_t(n));
+  c->inst_scale.assign(scale, scale + n);
+  c->selected = false;
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_select(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
+  if (!c) return V3DG_EINVAL;
+  CU(cudaSetDevice(c->device));
+  ST(setup_frame(c, cam, tau_px));
+  ST(enqueue_select(c));
+  c->selected = true;
+  c->rendered = false;
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_render(v3dg_ctx* c, float* rgb_out, float* t_out) {
+  if (!c) return V3DG_EINVAL;
+  if (!c->selected) return fail(c, V3DG_ENOTFOUND, "v3dg_render without a prior v3dg_select");
+  if (!rgb_out) return fail(c, V3DG_EINVAL, "rgb_out is NULL");
+  ST(run_frame(c, rgb_out, t_out));
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_render_host(v3dg_ctx* c, float* rgb_host, float* t_host) {
+  if (!c) return V3DG_EINVAL;
+  if (!c->selected) return fail(c, V3DG_ENOTFOUND, "v3dg_render_host without a prior v3dg_select");
+  if (!rgb_host) return fail(c, V3DG_EINVAL, "rgb_host is NULL");
+  const size_t px = size_t(c->cam.width) * size_t(c->cam.height);
+  ST(ensure(c, c->d_img, sizeof(float) * 3 * px));
+  if (t_host) ST(ensure(c, c->d_timg, sizeof(float) * px));
+  ST(run_frame(c, P<float>(c->d_img), t_host ? P<float>(c->d_timg) : nullptr));
+  CU(cudaMemcpyAsync(rgb_host, c->d_img.p, sizeof(float) * 3 * px, cudaMemcpyDeviceToHost, c->stream));
+  if (t_host) CU(cudaMemcpyAsync(t_host, c->d_timg.p, sizeof(float) * px, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (c->h_frame[kTimeout]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up; frame invalid");
+  if (c->h_frame[kOverflow]) return fail(c, V3DG_EOVERFLOW, "frame overflowed its buffers");
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_frame_stats(v3dg_ctx* c, v3dg_stats* out) {
+  if (!c || !out) return V3DG_EINVAL;
+  if (!c->selected) return fail(c, V3DG_ENOTFOUND, "no frame selected");
+  ST(sync_frame(c));
+  std::memset(out, 0, sizeof *out);
+  const uint32_t* f = c->h_frame;
+  out->render_nodes = f[kRenderNodes];
+  out->visible = f[kVisible];
+  out->pairs = f[kPairs];
+  out->overflow = f[kOverflow];
+  out->timeout = f[kTimeout];
+  uint32_t ncut = 0, ng = 0;
+  ST(run_cut(c, &ncut, &ng));
+  out->cut_nodes = ncut;
+  out->cut_gaussians = ng;
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_get_cut(v3dg_ctx* c, uint32_t* inst_node, uint64_t cap, uint64_t* n) {
+  if (!c || !n) return V3DG_EINVAL;
+  uint32_t ncut = 0, ng = 0;
+  ST(run_cut(c, &ncut, &ng));
+  *n = ncut;
+  if (inst_node && cap) {
+    const size_t m = size_t(std::min<uint64_t>(cap, ncut));
+    CU(cudaMemcpy(inst_node, c->d_cut.p, sizeof(uint2) * m, cudaMemcpyDeviceToHost));
+  }
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_get_projected(v3dg_ctx* c, uint64_t cap, uint64_t* n, uint32_t* inst, uint32_t* local, float* u,
+                               float* conic, float* opacity, float* rgb, uint32_t* depth_key, int32_t* rect) {
+  if (!c || !n) return V3DG_EINVAL;
+  if (!c->rendered) return fail(c, V3DG_ENOTFOUND, "no frame rendered");
+  ST(sync_frame(c));
+  const uint32_t nr = std::min(c->h_frame[kRenderNodes], c->cap_nodes);
+  const uint32_t nv = c->h_frame[kVisible];
+  const size_t S = size_t(nr) * kSlots;
+  std::vector<uint2> list(nr);
+  std::vector<uint32_t> keys(nv), slots(nv);
+  std::vector<float4> rec(3 * S);
+  std::vector<uint2> rc(S);
+  if (nr) CU(cudaMemcpy(list.data(), c->d_list.p, sizeof(uint2) * nr, cudaMemcpyDeviceToHost));
+  if (nv) {
+    CU(cudaMemcpy(keys.data(), (c->depth_in1 ? c->d_keys1 : c->d_keys0).p, 4 * size_t(nv), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(slots.data(), (c->depth_in1 ? c->d_vals1 : c->d_vals0).p, 4 * size_t(nv), cudaMemcpyDeviceToHost));
+  }
+  if (S) {
+    CU(cudaMemcpy(rec.data(), c->d_rec.p, sizeof(float4) * 3 * S, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(rc.data(), c->d_rect.p, sizeof(uint2) * S, cudaMemcpyDeviceToHost));
+  }
+  std::vector<uint32_t> order(nv);
+  for (uint32_t k = 0; k < nv; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return slots[a] < slots[b]; });
+  *n = nv;
+  const double log2e = 1.4426950408889634;
+  const uint64_t m = std::min<uint64_t>(cap, nv);
+  for (uint64_t q = 0; q < m; ++q) {
+    const uint32_t k = order[q];
+    const uint32_t slot = slots[k];
+    const uint2 e = list[slot / kSlots];
+    const uint32_t j = slot % kSlots;
+    const float4 r0 = rec[3 * size_t(slot)], r1 = rec[3 * size_t(slot) + 1], r2 = rec[3 * size_t(slot) + 2];
+    uint32_t org;
+    std::memcpy(&org, &r2.y, 4);
+    const uint2 rr = rc[slot];
+    if (inst) inst[q] = e.x;
+    if (local) local[q] = c->assets[c->inst_asset[e.x]].node_first[e.y] + j;
+    if (u) {
+      u[2 * q] = float(double(r0.x) + 16.0 * double(org & 0xFFFFu));
+      u[2 * q + 1] = float(double(r0.y) + 16.0 * double(org >> 16));
+    }
+    if (conic) {
+      conic[3 * q] = float(double(r0.z) / (-0.5 * log2e));
+      conic[3 * q + 1] = float(double(r0.w) / (-log2e));
+      conic[3 * q + 2] = float(double(r1.x) / (-0.5 * log2e));
+    }
+    if (opacity) opacity[q] = float(std::exp2(double(r1.y)));
+    if (rgb) {
+      rgb[3 * q] = r1.z;
+      rgb[3 * q + 1] = r1.w;
+      rgb[3 * q + 2] = r2.x;
+    }
+    if (depth_key) depth_key[q] = keys[k];
+    if (rect) {
+      rect[4 * q] = int32_t(rr.x & 0xFFFFu);
+      rect[4 * q + 1] = int32_t(rr.x >> 16);
+      rect[4 * q + 2] = int32_t(rr.y & 0xFFFFu);
+      rect[4 * q + 3] = int32_t(rr.y >> 16);
+    }
+  }
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_get_pairs(v3dg_ctx* c, uint64_t cap, uint64_t* n, uint32_t* tile, uint32_t* depth_key, uint32_t* inst,
+                           uint32_t* local) {
+  if (!c || !n) return V3DG_EINVAL;
+  if (!c->rendered) return fail(c, V3DG_ENOTFOUND, "no frame rendered");
+  ST(sync_frame(c));
+  const uint32_t np = std::min(c->h_frame[kPairsEff], c->cap_pairs);
+  const uint32_t nr = std::min(c->h_frame[kRenderNodes], c->cap_nodes);
+  const uint32_t nv = c->h_frame[kVisible];
+  *n = np;
+  const uint64_t m = std::min<uint64_t>(cap, np);
+  if (m == 0) return V3DG_OK;
+  std::vector<uint32_t> tk(m), tv(m), keys(nv), slots(nv);
+  std::vector<uint2> list(nr);
+  CU(cudaMemcpy(tk.data(), (c->tiles_in1 ? c->d_pk1 : c->d_pk0).p, 4 * m, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(tv.data(), (c->tiles_in1 ? c->d_pv1 : c->d_pv0).p, 4 * m, cudaMemcpyDeviceToHost));
+  if (nv) {
+    CU(cudaMemcpy(keys.data(), (c->depth_in1 ? c->d_keys1 : c->d_keys0).p, 4 * size_t(nv), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(slots.data(), (c->depth_in1 ? c->d_vals1 : c->d_vals0).p, 4 * size_t(nv), cudaMemcpyDeviceToHost));
+  }
+  if (nr) CU(cudaMemcpy(list.data(), c->d_list.p, sizeof(uint2) * nr, cudaMemcpyDeviceToHost));
+  std::vector<uint32_t> key_of(size_t(nr) * kSlots, 0xFFFFFFFFu);
+  for (uint32_t k = 0; k < nv; ++k)
+    if (slots[k] < key_of.size()) key_of[slots[k]] = keys[k];
+  for (uint64_t q = 0; q < m; ++q) {
+    const uint32_t slot = tv[q];
+    if (tile) tile[q] = tk[q];
+    if (slot / kSlots >= nr) return fail(c, V3DG_EINVAL, "pair %llu references slot %u beyond the render list",
+                                         (unsigned long long)q, slot);
+    const uint2 e = list[slot / kSlots];
+    if (depth_key) depth_key[q] = key_of[slot];
+    if (inst) inst[q] = e.x;
+    if (local) local[q] = c->assets[c->inst_asset[e.x]].node_first[e.y] + slot % kSlots;
+  }
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_get_tile_ranges(v3dg_ctx* c, uint32_t* range, uint64_t cap, uint64_t* n_tiles) {
+  if (!c || !n_tiles) return V3DG_EINVAL;
+  if (!c->rendered) return fail(c, V3DG_ENOTFOUND, "no frame rendered");
+  ST(sync_frame(c));
+  const uint64_t nt = uint64_t(c->cc.tiles_x) * uint64_t(c->cc.tiles_y);
+  *n_tiles = nt;
+  if (range && cap) CU(cudaMemcpy(range, c->d_ranges.p, sizeof(uint2) * std::min(cap, nt), cudaMemcpyDeviceToHost));
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_stage_times(v3dg_ctx* c, float* ms, int n, uint64_t* launches) {
+  if (!c) return V3DG_EINVAL;
+  if (launches) *launches = c->launches;
+  if (ms && n > 0) {
+    if (!c->stage_timing || !c->rendered) return fail(c, V3DG_ENOTFOUND, "stage timing is off or no frame rendered");
+    CU(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < n && i < kStages; ++i) CU(cudaEventElapsedTime(ms + i, c->ev[i], c->ev[i + 1]));
+  }
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_sort_pairs(v3dg_ctx* c, uint32_t* keys, uint32_t* vals, uint64_t n, int begin_bit, int end_bit) {
+  if (!c) return V3DG_EINVAL;
+  if (n == 0) return V3DG_OK;
+  if (!keys || !vals) return fail(c, V3DG_EINVAL, "NULL keys or values");
+  if (n > kMaxPairs) return fail(c, V3DG_EINVAL, "n = %llu exceeds %u", (unsigned long long)n, kMaxPairs);
+  if (begin_bit < 0 || end_bit > 32 || begin_bit >= end_bit) return fail(c, V3DG_EINVAL, "bad bit range [%d, %d)", begin_bit, end_bit);
+  CU(cudaSetDevice(c->device));
+  ST(ensure(c, c->d_sort_k, 4 * n));
+  ST(ensure(c, c->d_sort_v, 4 * n));
+  ST(ensure_status(c, ((n + kSortTile - 1) / kSortTile) * 256));
+  ST(ensure(c, c->d_hist, 4 * 256 * 4));
+  uint32_t* misc = P<uint32_t>(c->d_misc);  // [0] n, [1..4] tile counters, [5] timeout flag
+  CU(cudaMemsetAsync(misc, 0, sizeof(uint32_t) * 8, c->stream));
+  k_set_word<<<1, 1, 0, c->stream>>>(misc, uint32_t(n));
+  CU(cudaGetLastError());
+  bool in1 = false;
+  int nl = 0;
+  CU(launch_sort(keys, vals, P<uint32_t>(c->d_sort_k), P<uint32_t>(c->d_sort_v), misc, uint32_t(n), begin_bit, end_bit,
+                 false, sort_scratch(c, misc + 1), misc + 5, c->epoch, c->sm_count, c->stream, &in1, &nl));
+  next_epoch(c);
+  c->launches += nl + 1;
+  if (in1) {
+    CU(cudaMemcpyAsync(keys, c->d_sort_k.p, 4 * n, cudaMemcpyDeviceToDevice, c->stream));
+    CU(cudaMemcpyAsync(vals, c->d_sort_v.p, 4 * n, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  CU(cudaMemcpyAsync(c->h_tmp, misc + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (c->h_tmp[0]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up; output invalid");
+  c->err.clear();
+  return V3DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Internal layouts shared by the host side (v3dg_api.cpp) and the kernels (*.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace v3dg {
+
+constexpr int kTile = 16;              // 16x16 pixel tiles
+constexpr int kSlots = 64;             // Gaussian slots per cluster block on the device
+constexpr int kMaxShCoeffs = 16;       // degree 3
+
+// Attribute planes of one asset, each n_nodes * 64 floats (slot = node * 64 + j).
+enum AttrPlane : int {
+  kX = 0, kY, kZ, kOpacity, kLs0, kLs1, kLs2, kQw, kQx, kQy, kQz, kSh0,  // SH: kSh0 + 3 * coeff + channel
+};
+constexpr int attr_planes(int sh_coeffs) { return kSh0 + 3 * sh_coeffs; }
+
+// Node flags.
+constexpr uint8_t kLeaf = 1, kRoot = 2;
+
+struct AssetDev {
+  const float4* own;       // own sphere (cluster group of the node), asset frame
+  const float4* par;       // parent's own sphere (root: copy of own, unused)
+  const float4* bound;     // sphere around the node's Gaussian means: centre = their mean
+  const float* sigma_max;  // max over the node's Gaussians of exp(max log-scale)
+  const uint8_t* flags;    // kLeaf | kRoot
+  const uint8_t* count;    // Gaussians in the node, 1..64
+  const float* attr;       // attr_planes(sh_coeffs) planes of `stride` floats
+  uint32_t n_nodes;
+  uint32_t stride;         // n_nodes * 64
+  uint32_t sh_coeffs;      // (degree + 1)^2
+  uint32_t pad;
+};
+
+// Per (frame, instance) constants, computed on the host in FP64 (128-byte aligned, 256 B).
+struct alignas(16) InstFrame {
+  double m64[12];          // M = W [s R | t], row-major 3x4
+  float m[12];             // float32 rounding of m64
+  float cam_a[3];          // camera centre in the asset frame, R^T (C - t) / s
+  float s;                 // uniform scale
+  double s64;
+  float tau_f;             // area tolerance of this instance's asset
+  uint32_t asset;
+  uint32_t pad[20];
+};
+static_assert(sizeof(InstFrame) == 256, "InstFrame layout");
+
+// Camera constants passed by value to the kernels.
+struct CamConst {
+  float fx, fy, cx, cy;
+  float near_z;
+  float limx, limy;        // Jacobian clamp: 1.3 * (w / 2) / fx
+  int width, height;
+  int tiles_x, tiles_y;
+  double k_foot;           // pi * fx * fy (FP64) for the exact footprint re-test
+  float k_foot32;
+  float cull_kx, cull_ky;  // conservative pixel half-width factors of the visibility cull
+};
+
+// Frame counters (device, uint32 each).
+enum Counter : int {
+  kCutNodes = 0, kCutGauss, kRenderNodes, kVisible, kPairs, kOverflow, kTimeout,
+  kSlotCount = 7,          // render nodes (clamped) * 64: the slots the depth sort covers
+  kPairsEff = 8,           // pairs the tile sort / blend use: kPairs, or 0 when the frame overflowed
+  kNumCounters = 16,
+  kTileCounters = 16,      // [16, 48): atomic tile counters of the chained-scan kernels
+  kFrameWords = 48,
+};
+
+// Status words of the chained (decoupled look-back) scans: epoch << 34 | flag << 32 | value.
+constexpr uint64_t kFlagAgg = 1, kFlagPrefix = 2;
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+// ---------------------------------------------------------------- launch functions (return cudaError)
+// Selection (Sec. 3.3-3.4).  mode 0: render list (cut minus the visibility cull) + counters;
+// mode 1: the cut itself (parity read-back).
+cudaError_t launch_select(const InstFrame* inst, int n_inst, const AssetDev* assets, int node_blocks,
+                          const CamConst& cam, int mode, uint2* out, uint32_t cap, uint32_t* frame,
+                          uint32_t tile_counter_slot, uint64_t* status, uint32_t epoch, cudaStream_t st);
+
+// Per render-list node, FP64 reference for the projection (2 float4 per node):
+//   [0] = (U0 hi, U0 lo, V0 hi, V0 lo): pixel position of the node's mean centre as float pairs
+//   [1] = (rho_x, rho_y, Pz, mode): X/Z, Y/Z and Z of that centre in view space; mode 1 =
+//         compensated (centre well in front), 0 = direct (rho_x, rho_y then hold X, Y).
+cudaError_t launch_noderef(const uint2* render_list, uint32_t cap_nodes, const InstFrame* inst,
+                           const AssetDev* assets, const CamConst& cam, float4* ref,
+                           const uint32_t* frame, int sm_count, cudaStream_t st);
+
+// Records (3 float4 per slot, slot = render index * 64 + j):
+//   [0] = (u_rel, v_rel, na, nb), [1] = (nc, log2 o, r, g), [2] = (b, tile origin bits, 0, 0)
+// with (u_rel, v_rel) the 2D mean relative to the pixel origin of the Gaussian's first tile
+// (tx0, ty0) and log2(alpha) = na dx^2 + nb dx dy + nc dy^2 + log2 o.
+cudaError_t launch_project(const uint2* render_list, uint32_t cap_nodes, const InstFrame* inst,
+                           const AssetDev* assets, const CamConst& cam, const float4* ref, float4* rec,
+                           uint2* rect, uint32_t* keys, uint32_t* frame, int sm_count, cudaStream_t st);
+
+// Radix sort of (key, value) pairs, n read from *n_dev (clamped to cap).  Ping-pongs between
+// (k0, v0) and (k1, v1); the result lands in (k0, v0) when the pass count is even, else in
+// (k1, v1) -- *result_in_1 tells which.  implicit_vals: the values of the first pass are the
+// element indices (v0 is not read).
+struct SortScratch {
+  uint32_t* hist;          // 4 passes * 256
+  uint64_t* status;        // max_tiles * 256
+  uint32_t max_tiles;
+  uint32_t* tile_counters; // one per pass (zeroed by the caller's frame memset)
+};
+constexpr int kSortThreads = 256, kSortItems = 16, kSortTile = kSortThreads * kSortItems;
+cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
+                        uint32_t cap, int begin_bit, int end_bit, bool implicit_vals,
+                        const SortScratch& sc, uint32_t* err_flag, uint32_t& epoch, int sm_count,
+                        cudaStream_t st, bool* result_in_1, int* launches);
+
+// Pair offsets (exclusive scan of tile counts in depth order) and duplication.
+cudaError_t launch_pair_scan(const uint32_t* sorted_slots, const uint2* rect, uint32_t cap_slots,
+                             uint32_t* offsets, uint32_t* frame, uint32_t tile_counter_slot,
+                             uint64_t* status, uint32_t epoch, cudaStream_t st);
+cudaError_t launch_duplicate(const uint32_t* sorted_slots, const uint2* rect, const uint32_t* offsets,
+                             uint32_t cap_slots, uint32_t cap_pairs, int tiles_x, uint32_t* pair_keys,
+                             uint32_t* pair_vals, uint32_t* frame, int sm_count, cudaStream_t st);
+cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const uint32_t* frame,
+                          uint2* ranges, int n_tiles, int sm_count, cudaStream_t st);
+cudaError_t launch_blend(const uint2* ranges, const uint32_t* pair_vals, const float4* rec, uint32_t cap_slots,
+                         const CamConst& cam, float* rgb, float* t_out, cudaStream_t st);
+
+}  // namespace v3dg

@@ -350,3 +350,23 @@ def cached_asset(seed: int, n_leaves: int, cache_dir: str | None = None) -> Asse
                      if f.name != "gaussians_per_group"})
     os.replace(tmp, path)
     return a
+
+
+def _cached_asset_job(args):
+    seed, n_leaves, cache_dir = args
+    cached_asset(seed, n_leaves, cache_dir)
+    return seed
+
+
+def cached_assets(seeds, n_leaves: int, workers: int | None = None, cache_dir: str | None = None) -> list[Asset]:
+    """Several cached assets; missing ones are generated in parallel worker processes (spawned)."""
+    cache_dir = cache_dir or os.environ.get("V3DG_CACHE", "/tmp/v3dg_cache")
+    missing = [s for s in seeds
+               if not os.path.exists(os.path.join(cache_dir, f"asset_s{s}_n{n_leaves}_v1.npz"))]
+    if len(missing) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        workers = workers or min(len(missing), os.cpu_count() or 1)
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(_cached_asset_job, [(s, n_leaves, cache_dir) for s in missing]))
+    return [cached_asset(s, n_leaves, cache_dir) for s in seeds]

@@ -1,0 +1,170 @@
+"""GPU splatting (projection, binning + sort, blend) against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import scenes
+from v3dg_cases import (IMG_ABS, PSNR_MIN, assert_cut_parity, assert_pairs_parity, assert_projection_parity,
+                        image_errors)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Context():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2505_06523_gb300 import Context
+    return Context
+
+
+def _frame(Context, assets, inst, cam, tau, opts=None):
+    with Context(0) as ctx:
+        for k, v in (opts or {}).items():
+            ctx.set_option(k, v)
+        for a in assets:
+            ctx.load_hierarchy(a)
+        ctx.set_instances(inst)
+        ctx.select(cam, tau)
+        rgb, T = ctx.render(want_T=True)
+        out = {"rgb": rgb.cpu().numpy(), "T": T.cpu().numpy(), "cut": ctx.get_cut(), "proj": ctx.get_projected(),
+               "pairs": ctx.get_pairs(), "ranges": ctx.tile_ranges(), "stats": ctx.frame_stats()}
+    return out
+
+
+def _check_ranges(out, cam):
+    pr, rg = out["pairs"], out["ranges"]
+    n_tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    assert rg.shape == (n_tiles, 2)
+    for t in np.unique(pr["tile"]):
+        s, e = rg[t]
+        assert (pr["tile"][s:e] == t).all() and (s == 0 or pr["tile"][s - 1] != t) and (e == len(pr["tile"]) or pr["tile"][e] != t)
+    empty = np.setdiff1d(np.arange(n_tiles), np.unique(pr["tile"]))
+    assert (rg[empty, 0] == rg[empty, 1]).all()
+
+
+def test_tiny_full_parity(Context, tiny_asset):
+    """100k-leaf asset, 256x256, tau = 1 px: cut, records, pairs, ranges and the whole image."""
+    cam = scenes.tiny_camera()
+    inst = scenes.single_instance()
+    out = _frame(Context, [tiny_asset], inst, cam, 1.0)
+    cut = oracle.select([tiny_asset], inst, cam, 1.0)
+    assert_cut_parity(out["cut"], cut)
+    p = oracle.project([tiny_asset], inst, cam, cut)
+    assert_projection_parity(out["proj"], p)
+    assert_pairs_parity(out["pairs"], p, cam)
+    _check_ranges(out, cam)
+    C, T, B = oracle.render_image(p, cam.width, cam.height)
+    err, ps, nb = image_errors(out["rgb"], C, B)
+    assert err <= IMG_ABS, f"max |err| {err} over {cam.width * cam.height - nb} pixels"
+    assert ps >= PSNR_MIN
+    assert np.abs(out["T"].astype(np.float64) - T)[~B].max() <= IMG_ABS
+
+
+def test_tiny_other_views(Context, tiny_asset):
+    inst = scenes.single_instance()
+    for cam, tau in [(scenes.look_at((1.2, -1.6, 0.9), (0, 0, 0), 200, 136, 70.0), 0.5),
+                     (scenes.look_at((0.3, 0.2, 2.2), (0, 0, 0), 97, 75, 50.0), 2.0),
+                     (scenes.look_at((0.0, -1.15, 0.0), (0, 1, 0.2), 160, 120, 90.0), 1.0)]:
+        out = _frame(Context, [tiny_asset], inst, cam, tau)
+        cut = oracle.select([tiny_asset], inst, cam, tau)
+        assert_cut_parity(out["cut"], cut)
+        p = oracle.project([tiny_asset], inst, cam, cut)
+        assert_projection_parity(out["proj"], p)
+        assert_pairs_parity(out["pairs"], p, cam)
+        C, T, B = oracle.render_image(p, cam.width, cam.height)
+        err, ps, _ = image_errors(out["rgb"], C, B)
+        assert err <= IMG_ABS and ps >= PSNR_MIN, (err, ps)
+
+
+def test_single_gaussian_closed_form(Context):
+    """One isotropic Gaussian on the optical axis renders c * min(0.999, o exp(-r^2 / (2 s^2)))."""
+    from test_oracle_splat import cam_identity, one_node_asset
+    sigma, z, f, o = 0.04, 3.0, 50.0, 0.7
+    sh = np.zeros((1, 16, 3))
+    sh[0, 0] = [0.4, -0.2, 0.1]
+    a = one_node_asset([[0, 0, z]], [[math.log(sigma)] * 3], opacity=[o], sh=sh)
+    cam = cam_identity(w=40, h=36, f=f)
+    out = _frame(Context, [a], scenes.single_instance(), cam, 1.0)
+    s = f * math.exp(float(np.float32(math.log(sigma)))) / z
+    ys, xs = np.mgrid[0:36, 0:40]
+    r2 = (xs + 0.5 - 20.0) ** 2 + (ys + 0.5 - 18.0) ** 2
+    al = np.minimum(0.999, float(np.float32(o)) * np.exp(-r2 / (2 * s * s)))
+    near = np.abs(al - 1 / 255) <= 1e-3 / 255
+    al = np.where(al >= 1 / 255, al, 0.0)
+    col = 0.5 + sh[0, 0].astype(np.float32).astype(np.float64) * 0.5 / math.sqrt(math.pi)
+    err = np.abs(out["rgb"] - al[..., None] * col).max(axis=-1)
+    assert err[~near].max() <= IMG_ABS
+    assert np.abs(out["T"] - (1 - al))[~near].max() <= IMG_ABS
+
+
+def test_crowd_decimated_pixels(Context, tiny_asset, small_asset):
+    """A 200-instance composition at 640x360: full-image parity."""
+    inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+    assets = [tiny_asset, small_asset]
+    cam = scenes.crowd_camera(40, 640, 360)
+    out = _frame(Context, assets, inst, cam, 1.0)
+    cut = oracle.select(assets, inst, cam, 1.0)
+    assert_cut_parity(out["cut"], cut)
+    p = oracle.project(assets, inst, cam, cut)
+    assert_projection_parity(out["proj"], p)
+    assert_pairs_parity(out["pairs"], p, cam)
+    C, T, B = oracle.render_image(p, cam.width, cam.height)
+    err, ps, nb = image_errors(out["rgb"], C, B)
+    assert err <= IMG_ABS and ps >= PSNR_MIN, (err, ps, nb)
+
+
+def test_orbit_sampled_pixels(Context):
+    """1M-leaf asset at 1920x1080, near / mid / far: sampled pixels against the per-pixel oracle."""
+    from synth.assets import cached_asset
+    asset = cached_asset(1, 1_000_000)
+    inst = scenes.single_instance()
+    rng = np.random.default_rng(0)
+    for k in (0, 3, 7):
+        cam = scenes.orbit_camera(scenes.orbit_distances()[k])
+        out = _frame(Context, [asset], inst, cam, 1.0)
+        cut = oracle.select([asset], inst, cam, 1.0)
+        assert_cut_parity(out["cut"], cut)
+        p = oracle.project([asset], inst, cam, cut)
+        assert_projection_parity(out["proj"], p)
+        # pixels where something is drawn, plus a few random ones
+        drawn = np.argwhere(out["T"] < 0.999)
+        pick = drawn[rng.choice(len(drawn), size=min(48, len(drawn)), replace=False)] if len(drawn) else np.zeros((0, 2), int)
+        pix = [(int(x), int(y)) for y, x in pick] + [(int(rng.integers(0, 1920)), int(rng.integers(0, 1080))) for _ in range(8)]
+        c, t, b = oracle.render_pixels(p, pix)
+        g = np.array([out["rgb"][y, x] for x, y in pix], np.float64)
+        e = np.abs(g - c).max(axis=1)
+        assert e[~b].max() <= IMG_ABS, (k, e.max())
+
+
+def test_growth_from_tiny_capacities(Context, tiny_asset):
+    """Start with 64-node / 4096-pair buffers: the frame overflows, grows and matches."""
+    from paper_2505_06523_gb300._native import V3DG_OPT_CAP_NODES, V3DG_OPT_CAP_PAIRS
+    cam = scenes.tiny_camera()
+    inst = scenes.single_instance()
+    small = _frame(Context, [tiny_asset], inst, cam, 1.0, {V3DG_OPT_CAP_NODES: 64, V3DG_OPT_CAP_PAIRS: 4096})
+    big = _frame(Context, [tiny_asset], inst, cam, 1.0)
+    assert (small["rgb"] == big["rgb"]).all()
+    assert small["stats"]["overflow"] == 0
+
+
+def test_render_host_matches_device(Context, tiny_asset):
+    cam = scenes.tiny_camera()
+    with Context(0) as ctx:
+        ctx.load_hierarchy(tiny_asset)
+        ctx.set_instances(scenes.single_instance())
+        ctx.select(cam, 1.0)
+        rgb_d, t_d = ctx.render(want_T=True)
+        rgb_h, t_h = ctx.render_host(want_T=True)
+    assert (rgb_d.cpu().numpy() == rgb_h).all() and (t_d.cpu().numpy() == t_h).all()
+
+
+def test_deterministic_repeat(Context, tiny_asset, small_asset):
+    inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+    cam = scenes.crowd_camera(150, 480, 270)
+    a = _frame(Context, [tiny_asset, small_asset], inst, cam, 1.0)
+    b = _frame(Context, [tiny_asset, small_asset], inst, cam, 1.0)
+    assert (a["rgb"] == b["rgb"]).all()
+    assert all((a["pairs"][k] == b["pairs"][k]).all() for k in a["pairs"])
