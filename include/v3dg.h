@@ -181,6 +181,25 @@ v3dg_status v3dg_stage_times(v3dg_ctx* ctx, float* ms, int n, uint64_t* launches
 v3dg_status v3dg_sort_pairs(v3dg_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t n,
                             int begin_bit, int end_bit);
 
+/* Largest n that v3dg_sort_pairs_noalloc accepts (its fixed scratch holds this many pairs). */
+#define V3DG_SORT_NOALLOC_MAX_PAIRS (1u << 20)
+
+/* The same stable radix sort as v3dg_sort_pairs, for callers that cannot allocate device memory
+ * (the paper has no counterpart: this serves hosts that own every device allocation themselves,
+ * such as an engine that reserves its pools at start-up, or a real-time loop where cudaMalloc /
+ * cudaFree would stall a frame).  It allocates nothing and needs no context: its scratch is one
+ * fixed device array of the library, sized for V3DG_SORT_NOALLOC_MAX_PAIRS pairs (about 8.5 MB),
+ * held by every GPU that loads the library until the process exits.
+ *  - keys, vals: device pointers of the calling thread's current device, n uint32 each, sorted in
+ *    place on key bits [begin_bit, end_bit); cuda_stream: a stream of that device (NULL: legacy).
+ *  - n > V3DG_SORT_NOALLOC_MAX_PAIRS returns V3DG_EOVERFLOW and does nothing; bad pointers or
+ *    bit ranges return V3DG_EINVAL; a bounded device wait that gave up returns V3DG_ETIMEOUT.
+ *  - Synchronises cuda_stream before returning.  The first call on a device looks up the scratch
+ *    array's address (make it before any stream capture).  All calls share the one array: calls
+ *    whose work overlaps on the GPU race with each other. */
+v3dg_status v3dg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, uint64_t n, int begin_bit, int end_bit,
+                                    void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ SIGNATURES = {
     "v3dg_get_tile_ranges": (_I32, [_P, _P, _U64, ctypes.POINTER(_U64)]),
     "v3dg_stage_times": (_I32, [_P, _P, _I32, ctypes.POINTER(_U64)]),
     "v3dg_sort_pairs": (_I32, [_P, _P, _P, _U64, _I32, _I32]),
+    "v3dg_sort_pairs_noalloc": (_I32, [_P, _P, _U64, _I32, _I32, _P]),
 }
 
 _lib = None
@@ -199,3 +200,11 @@ def v3dg_stage_times(ctx, ms_ptr: int | None, n: int) -> int:
 
 def v3dg_sort_pairs(ctx, keys_ptr: int, vals_ptr: int, n: int, begin_bit: int, end_bit: int) -> None:
     _check(ctx, lib().v3dg_sort_pairs(ctx, _P(keys_ptr), _P(vals_ptr), n, begin_bit, end_bit))
+
+
+def v3dg_sort_pairs_noalloc(keys_ptr: int, vals_ptr: int, n: int, begin_bit: int, end_bit: int,
+                            stream_ptr: int | None = None) -> None:
+    st = lib().v3dg_sort_pairs_noalloc(_P(keys_ptr), _P(vals_ptr), n, begin_bit, end_bit,
+                                       _P(stream_ptr) if stream_ptr else None)
+    if st != V3DG_OK:
+        raise V3dgError(st, f"v3dg_sort_pairs_noalloc(n={n}, bits [{begin_bit}, {end_bit}))")

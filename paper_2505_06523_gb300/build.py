@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libv3dg.so")
-SOURCES = ["v3dg_api.cu", "k_select.cu", "k_project.cu", "k_sort.cu", "k_bin.cu", "k_blend.cu"]
+SOURCES = ["v3dg_api.cu", "k_select.cu", "k_project.cu", "k_sort.cu", "k_bin.cu", "k_blend.cu", "v3dg_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
