@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--tau", type=float, default=TAU_PX)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--assets", type=int, default=N_ASSETS, help="fewer assets: a smaller case for profiling")
+    ap.add_argument("--instances", type=int, default=N_INST, help="fewer instances: a smaller case for profiling")
     return ap.parse_args()
 
 
@@ -52,11 +54,11 @@ def dist_env():
     return rank, world, local
 
 
-def load_scene():
+def load_scene(n_assets=N_ASSETS, n_inst=N_INST):
     from synth import scenes
     from synth.assets import cached_assets
-    assets = cached_assets(list(range(N_ASSETS)), N_LEAVES)
-    inst = scenes.crowd_instances(N_INST, n_assets=N_ASSETS)
+    assets = cached_assets(list(range(n_assets)), N_LEAVES)
+    inst = scenes.crowd_instances(n_inst, n_assets=n_assets)
     return assets, inst
 
 
@@ -194,7 +196,7 @@ def main():
     from paper_2505_06523_gb300 import _native as N
     from synth import scenes
 
-    assets, inst = load_scene()
+    assets, inst = load_scene(args.assets, args.instances)
     ctx = Context(local)
     for a in assets:
         ctx.load_hierarchy(a)
@@ -204,9 +206,13 @@ def main():
     rgb = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32, device=f"cuda:{local}")
     stream = ctx.stream
 
-    # warm-up with checked frames: grows the buffers, then run fully asynchronously
+    # warm-up with checked frames, then one untimed checked pass over the frames the timed region
+    # will render, so that every buffer has grown to its size; then run fully asynchronously
     for s in range(args.warmup):
         ctx.select(cams[frame_ids[s]], args.tau)
+        ctx.render(rgb)
+    for fid in sorted(set(frame_ids[args.warmup:])):
+        ctx.select(cams[fid], args.tau)
         ctx.render(rgb)
     ctx.set_option(N.V3DG_OPT_SYNC_CHECK, 0)
 
@@ -247,6 +253,13 @@ def main():
     ctx.set_option(N.V3DG_OPT_STAGE_TIMING, 0)
     stage_ms = {k: float(np.median([r[i] for r in stage_runs])) for i, k in enumerate(STAGES)}
     fs = ctx.frame_stats()
+    # the blend's work on the last of those frames (a separate, counting run of the same frame)
+    ctx.set_option(N.V3DG_OPT_COUNT_WORK, 1)
+    ctx.select(cams[frame_ids[4]], args.tau)
+    ctx.render(rgb)
+    work = ctx.frame_stats()
+    ctx.set_option(N.V3DG_OPT_COUNT_WORK, 0)
+    fs["blend_evals"], fs["blend_contribs"] = work["blend_evals"], work["blend_contribs"]
 
     # e2e through the public API with host buffers: per step, the instance table (host FP64) goes
     # in, the camera is set, and the RGB image comes back into pinned host memory
@@ -267,12 +280,12 @@ def main():
         t = torch.tensor([e2e_s], dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_val = world * e2e_steps / float(t.item())
-    h2d = N_INST * 256
+    h2d = inst.n * 256
     d2h = WIDTH * HEIGHT * 3 * 4
 
     peaks, peak_kind = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
-    roofline = roofline_for(dom, stage_ms, fs, peaks, peak_kind)
+    roofline = roofline_for(dom, stage_ms, fs, peaks, peak_kind, stage_runs[-1])
 
     line = None
     if rank == 0:
@@ -285,14 +298,17 @@ def main():
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tau_px": args.tau, "path": "plain FP32, one frame at a time",
+            "config": {"workload": WORKLOAD if (args.assets, args.instances) == (N_ASSETS, N_INST) else
+                       f"profiling case: {args.assets} assets, {args.instances} instances", "tau_px": args.tau,
+                       "path": "plain FP32, one frame at a time",
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (3.1 GB of attributes; "
                        "per-frame gathers of the selected Gaussians exceed the 129 MB L2)"},
             "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "stages_ms": stage_ms,
-            "frame": {k: int(fs[k]) for k in ("cut_nodes", "cut_gaussians", "render_nodes", "visible", "pairs")},
+            "frame": {k: int(fs[k]) for k in ("cut_nodes", "cut_gaussians", "render_nodes", "visible", "pairs",
+                                              "blend_evals", "blend_contribs")},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
@@ -303,8 +319,27 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def roofline_for(stage, stage_ms, fs, peaks, peak_kind):
-    """Algorithmic bytes per launch of the dominant stage over its measured duration."""
+# FP32 lanes of the GB300 (152 SMs x 128) at the maximum SM clock: the issue peak of the blend
+FP32_LANES = 152 * 128
+# algorithmic FP32 operations of the blend: per (pixel, Gaussian) evaluated inside the Gaussian's
+# pixel box (dx, dy, the quadratic form, the skip test) and per contribution (exp2, clamp, skip
+# test, 1 - alpha, T update, stop test, weight, three colour FMAs)
+BLEND_OPS_EVAL, BLEND_OPS_CONTRIB = 8, 10
+
+
+def roofline_for(stage, stage_ms, fs, peaks, peak_kind, last_ms=None):
+    """Algorithmic work per launch of the dominant stage over its measured duration."""
+    if stage == "blend" and fs.get("blend_evals"):
+        ms = last_ms[STAGES.index("blend")] if last_ms else stage_ms["blend"]
+        ops = BLEND_OPS_EVAL * fs["blend_evals"] + BLEND_OPS_CONTRIB * fs["blend_contribs"]
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = FP32_LANES * mhz * 1e6 / 1e12
+        achieved = ops / (ms / 1000.0) / 1e12
+        return {"stage": "blend", "kernel": "k_blend", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: {FP32_LANES} FP32 lanes x {mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+                "work": {"evals": fs["blend_evals"], "contribs": fs["blend_contribs"],
+                         "ops_per_eval": BLEND_OPS_EVAL, "ops_per_contrib": BLEND_OPS_CONTRIB, "ms": ms}}
     vis, pairs, nodes = fs["visible"], fs["pairs"], fs["render_nodes"]
     slots = nodes * 64
     bytes_per = {

@@ -95,6 +95,9 @@ typedef struct {
   uint64_t pairs;           /* (tile, Gaussian) pairs sorted and blended */
   uint32_t overflow;        /* nonzero if a capacity was exceeded (outputs invalid) */
   uint32_t timeout;         /* nonzero if a bounded device wait gave up (outputs invalid) */
+  uint64_t blend_evals;     /* (pixel, Gaussian) pairs the blend evaluated inside the Gaussian's
+                               pixel box (only with V3DG_OPT_COUNT_WORK, else 0) */
+  uint64_t blend_contribs;  /* of those, the ones with alpha >= 1/255 that were blended */
 } v3dg_stats;
 
 /* Options for v3dg_set_option. */
@@ -104,7 +107,8 @@ enum {
                                checks v3dg_frame_stats */
   V3DG_OPT_STAGE_TIMING = 2, /* 1: record CUDA events around every stage (see v3dg_stage_times) */
   V3DG_OPT_CAP_NODES = 3,    /* current render-list capacity in clusters (>= 64); grows on demand */
-  V3DG_OPT_CAP_PAIRS = 4     /* current (tile, Gaussian) pair capacity (>= 4096); grows on demand */
+  V3DG_OPT_CAP_PAIRS = 4,    /* current (tile, Gaussian) pair capacity (>= 4096); grows on demand */
+  V3DG_OPT_COUNT_WORK = 5    /* 1: the blend also counts its evaluations (v3dg_stats.blend_*) */
 };
 
 /* Create a context on CUDA device `device`.  `alloc` may be NULL (cudaMalloc/cudaFree). */

@@ -19,6 +19,7 @@ V3DG_OPT_SYNC_CHECK = 1
 V3DG_OPT_STAGE_TIMING = 2
 V3DG_OPT_CAP_NODES = 3
 V3DG_OPT_CAP_PAIRS = 4
+V3DG_OPT_COUNT_WORK = 5
 
 
 class V3dgError(RuntimeError):
@@ -53,7 +54,8 @@ class v3dg_hierarchy_desc(ctypes.Structure):
 class v3dg_stats(ctypes.Structure):
     _fields_ = [("cut_nodes", ctypes.c_uint64), ("cut_gaussians", ctypes.c_uint64),
                 ("render_nodes", ctypes.c_uint64), ("visible", ctypes.c_uint64), ("pairs", ctypes.c_uint64),
-                ("overflow", ctypes.c_uint32), ("timeout", ctypes.c_uint32)]
+                ("overflow", ctypes.c_uint32), ("timeout", ctypes.c_uint32),
+                ("blend_evals", ctypes.c_uint64), ("blend_contribs", ctypes.c_uint64)]
 
 
 _P = ctypes.c_void_p

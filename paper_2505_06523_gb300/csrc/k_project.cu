@@ -211,7 +211,8 @@ k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* _
       float4* rp = rec + 3 * slot;
       rp[0] = make_float4(u_rel, v_rel, -0.5f * kLog2e * ia, -kLog2e * ib);
       rp[1] = make_float4(-0.5f * kLog2e * ic, log2f(op), col[0], col[1]);
-      rp[2] = make_float4(col[2], __uint_as_float(origin), 0.f, 0.f);
+      rp[2] = make_float4(col[2], __uint_as_float(origin), __uint_as_float(uint32_t(x0) | (uint32_t(x1) << 16)),
+                          __uint_as_float(uint32_t(y0) | (uint32_t(y1) << 16)));
       rect[slot] = make_uint2(uint32_t(tx0) | (uint32_t(tx1) << 16), uint32_t(ty0) | (uint32_t(ty1) << 16));
       keys[slot] = __float_as_uint(z32);
       ++nvis;

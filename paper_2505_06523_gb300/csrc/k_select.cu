@@ -1,15 +1,18 @@
 // Selection: per-(instance, cluster) footprints and the cut predicate F_c <= tau < F_p
 // (Sec. 3.3 Fig. 4, Sec. 3.4), with stable stream compaction of the cut in (instance, node) order.
 //
-// One thread per (instance, node); a block covers 256 nodes of one instance.  Blocks take
-// virtual tile ids from an atomic counter, compact their selected nodes with a block scan and
-// find their output offset with a bounded decoupled look-back, so the cut is written in one pass.
+// A block covers 2048 consecutive nodes of one instance, 8 per thread (node = base + i * 256 +
+// thread).  Blocks take virtual tile ids from an atomic counter, compact their selected nodes in
+// (item, warp, lane) order -- which is node order -- and find their output offset with a bounded
+// decoupled look-back, so the cut is written in one pass.
 #include "dev_common.cuh"
 
 namespace v3dg {
 namespace {
 
 constexpr int kSelThreads = 256;
+constexpr int kSelItems = 8;
+constexpr int kSelWarps = kSelThreads / 32;
 constexpr float kEps = 5.9604645e-08f;  // 2^-24
 
 // F(sphere) <= tau for one asset-space sphere (c, r) under instance I, where
@@ -83,9 +86,10 @@ __global__ void __launch_bounds__(kSelThreads)
 k_select(const InstFrame* __restrict__ inst, int n_inst, const AssetDev* __restrict__ assets, int node_blocks,
          CamConst cam, int mode, uint2* __restrict__ out, uint32_t cap, uint32_t* __restrict__ frame,
          uint32_t tc_slot, uint64_t* __restrict__ status, uint32_t epoch) {
-  __shared__ uint32_t s_tile, s_excl;
-  __shared__ uint32_t s_scan[kSelThreads / 32 + 1];
-  __shared__ uint32_t s_gauss[kSelThreads / 32];
+  __shared__ uint32_t s_tile, s_excl, s_total;
+  __shared__ uint32_t s_cnt[kSelItems * kSelWarps];   // per (item, warp): selected count, then offset
+  __shared__ uint32_t s_gauss[kSelWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_tile = atomicAdd(frame + kTileCounters + tc_slot, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
@@ -94,44 +98,67 @@ k_select(const InstFrame* __restrict__ inst, int n_inst, const AssetDev* __restr
   const uint32_t ii = tile / node_blocks, nb = tile % node_blocks;
   const InstFrame& I = inst[ii];
   const AssetDev& A = assets[I.asset];
-  const uint32_t node = nb * kSelThreads + threadIdx.x;
-  bool keep = false;
-  uint32_t gcount = 0;
-  if (node < A.n_nodes) {
-    const uint8_t fl = A.flags[node];
-    const float tau = I.tau_f;
-    const bool own_ok = (fl & kLeaf) || footprint_le(A.own[node], I, cam, tau);
-    const bool sel = own_ok && ((fl & kRoot) || !footprint_le(A.par[node], I, cam, tau));
-    if (sel) {
-      gcount = A.count[node];
-      keep = (mode == 1) || !cull_node(A.bound[node], A.sigma_max[node], I, cam);
+  const float tau = I.tau_f;
+  uint32_t keepmask = 0, gsum = 0;
+#pragma unroll
+  for (int i = 0; i < kSelItems; ++i) {
+    const uint32_t node = nb * (kSelThreads * kSelItems) + i * kSelThreads + threadIdx.x;
+    bool keep = false;
+    if (node < A.n_nodes) {
+      const uint8_t fl = A.flags[node];
+      const bool own_ok = (fl & kLeaf) || footprint_le(A.own[node], I, cam, tau);
+      const bool sel = own_ok && ((fl & kRoot) || !footprint_le(A.par[node], I, cam, tau));
+      if (sel) {
+        keep = (mode == 1) || !cull_node(A.bound[node], A.sigma_max[node], I, cam);
+        if (mode == 1) gsum += A.count[node];
+      }
     }
+    const uint32_t b = __ballot_sync(0xffffffffu, keep);
+    if (keep) keepmask |= 1u << i;
+    if (lane == 0) s_cnt[i * kSelWarps + warp] = __popc(b);
   }
   if (mode == 1) {  // Gaussians in the cut, one atomic per block
-    uint32_t g = keep ? gcount : 0u;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) g += __shfl_xor_sync(0xffffffffu, g, d);
-    if ((threadIdx.x & 31) == 0) s_gauss[threadIdx.x >> 5] = g;
+    for (int d = 16; d > 0; d >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, d);
+    if (lane == 0) s_gauss[warp] = gsum;
   }
-  uint32_t total;
-  const uint32_t rank = block_exclusive_scan<kSelThreads / 32>(keep ? 1u : 0u, s_scan, &total);
-  if (threadIdx.x == 0) {
-    s_excl = chained_exclusive(status, 1, tile, total, epoch, frame + kTimeout);
-    if (mode == 1) {
-      uint32_t g = 0;
-      for (int w = 0; w < kSelThreads / 32; ++w) g += s_gauss[w];
-      if (g) atomicAdd(frame + kCutGauss, g);
+  __syncthreads();
+  if (warp == 0) {  // exclusive scan of the 64 (item, warp) counts in that order
+    const uint32_t a = s_cnt[2 * lane], b = s_cnt[2 * lane + 1];
+    uint32_t incl = a + b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const uint32_t ex = incl - a - b;
+    s_cnt[2 * lane] = ex;
+    s_cnt[2 * lane + 1] = ex + a;
+    if (lane == 31) {
+      s_total = incl;
+      s_excl = chained_exclusive(status, 1, tile, incl, epoch, frame + kTimeout);
+      if (mode == 1) {
+        uint32_t g = 0;
+        for (int w = 0; w < kSelWarps; ++w) g += s_gauss[w];
+        if (g) atomicAdd(frame + kCutGauss, g);
+      }
     }
   }
   __syncthreads();
-  const uint32_t pos = s_excl + rank;
-  if (keep) {
-    if (pos < cap)
-      out[pos] = make_uint2(ii, node);
-    else
-      atomicOr(frame + kOverflow, 1u);
+#pragma unroll
+  for (int i = 0; i < kSelItems; ++i) {
+    const bool keep = (keepmask >> i) & 1u;
+    const uint32_t b = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const uint32_t pos = s_excl + s_cnt[i * kSelWarps + warp] + __popc(b & lanemask_lt());
+      const uint32_t node = nb * (kSelThreads * kSelItems) + i * kSelThreads + threadIdx.x;
+      if (pos < cap)
+        out[pos] = make_uint2(ii, node);
+      else
+        atomicOr(frame + kOverflow, 1u);
+    }
   }
-  if (threadIdx.x == 0 && tile == ntiles - 1) frame[mode == 0 ? kRenderNodes : kCutNodes] = s_excl + total;
+  if (threadIdx.x == 0 && tile == ntiles - 1) frame[mode == 0 ? kRenderNodes : kCutNodes] = s_excl + s_total;
 }
 
 }  // namespace

@@ -14,25 +14,37 @@ namespace {
 constexpr int kBins = 256;
 constexpr int kWarps = kSortThreads / 32;
 
+// Digit counts of every pass in one read of the keys.  Keys are often concentrated in a few
+// digits (the high bytes of float depths), so equal digits within a warp are combined first
+// (match + popc) and counted with one shared atomic, into per-warp sub-histograms.
 __global__ void __launch_bounds__(256)
 k_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev, uint32_t cap, int begin_bit,
        int end_bit, int passes, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t sh[4][kBins];
-  for (int i = threadIdx.x; i < 4 * kBins; i += blockDim.x) sh[i / kBins][i % kBins] = 0;
+  __shared__ uint32_t sh[8][4][kBins];
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < 8 * 4 * kBins; i += blockDim.x) (&sh[0][0][0])[i] = 0;
   __syncthreads();
   const uint32_t n = min(*n_dev, cap);
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint32_t k = keys[i];
+  const uint32_t n_round = (n + 31u) & ~31u;   // whole warps iterate together
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+    const bool ok = i < n;
+    const uint32_t k = ok ? keys[i] : 0u;
+    const uint32_t live = __ballot_sync(0xffffffffu, ok);
+    if (!ok) continue;
     for (int p = 0; p < passes; ++p) {
       const int sh_ = begin_bit + 8 * p;
       const uint32_t m = end_bit - sh_ >= 8 ? 0xFFu : ((1u << (end_bit - sh_)) - 1u);
-      atomicAdd(&sh[p][(k >> sh_) & m], 1u);
+      const uint32_t d = (k >> sh_) & m;
+      const uint32_t peers = __match_any_sync(live, d);
+      if ((peers & lanemask_lt()) == 0) atomicAdd(&sh[warp][p][d], __popc(peers));
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * kBins; i += blockDim.x) {
-    const uint32_t c = sh[i / kBins][i % kBins];
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) c += sh[w][i / kBins][i % kBins];
     if (c) atomicAdd(hist + i, c);
   }
 }

@@ -67,7 +67,7 @@ struct v3dg_ctx {
   cudaEvent_t ev_inst = nullptr;
   DevBuf d_frame, d_cutframe, d_misc;
   uint32_t* h_frame = nullptr;   // pinned copy of the frame words, written at the end of each frame
-  uint32_t* h_tmp = nullptr;     // pinned scratch words
+  uint32_t* h_tmp = nullptr;     // pinned scratch: [0, 48) frame words of read-backs, [48, 52) blend work
 
   uint32_t cap_nodes = 0, cap_slots = 0, cap_pairs = 0, status_words = 0, cap_cut = 0;
   DevBuf d_list, d_ref, d_keys0, d_keys1, d_vals0, d_vals1, d_rec, d_rect, d_off;
@@ -76,7 +76,8 @@ struct v3dg_ctx {
   bool depth_in1 = false, tiles_in1 = false;
   uint32_t epoch = 1;
   uint64_t launches = 0;
-  bool sync_check = true, stage_timing = false;
+  bool sync_check = true, stage_timing = false, count_work = false;
+  unsigned long long work[2] = {0, 0};
   cudaEvent_t ev[kStages + 1] = {};
 };
 
@@ -243,7 +244,7 @@ v3dg_status setup_frame(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
 
   uint32_t max_nodes = 0;
   for (auto& a : c->assets) max_nodes = std::max(max_nodes, a.n_nodes);
-  c->node_blocks = int((max_nodes + 255) / 256);
+  c->node_blocks = int((max_nodes + 2047) / 2048);   // k_select covers 2048 nodes per block
   c->n_inst_frame = n;
 
   // the pinned staging buffer is reused: wait until the previous upload out of it has completed
@@ -362,8 +363,13 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
   c->launches += 1;
 
   stage_event(c, kStageBlend);
-  CU(launch_blend(P<uint2>(c->d_ranges), tv, P<float4>(c->d_rec), c->cap_slots, k, rgb, t_out, c->stream));
+  // d_misc: [0..7] the standalone sort's words, [8..11] two 64-bit blend work counters
+  unsigned long long* work = c->count_work ? reinterpret_cast<unsigned long long*>(P<uint32_t>(c->d_misc) + 8) : nullptr;
+  if (work) CU(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), c->stream));
+  CU(launch_blend(P<uint2>(c->d_ranges), tv, P<float4>(c->d_rec), c->cap_slots, k, rgb, t_out, work, c->stream));
   c->launches += 1;
+  if (work)
+    CU(cudaMemcpyAsync(c->h_tmp + kFrameWords, work, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   stage_event(c, kStages);
   CU(cudaMemcpyAsync(c->h_frame, c->d_frame.p, sizeof(uint32_t) * kFrameWords, cudaMemcpyDeviceToHost, c->stream));
   c->rendered = true;
@@ -492,7 +498,7 @@ v3dg_status v3dg_create(int device, const v3dg_allocator* alloc, v3dg_ctx** out)
   if (cudaSetDevice(device) != cudaSuccess) return bail(V3DG_ECUDA);
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return bail(V3DG_ECUDA);
   if (cudaMallocHost(&c->h_frame, sizeof(uint32_t) * kFrameWords) != cudaSuccess) return bail(V3DG_ECUDA);
-  if (cudaMallocHost(&c->h_tmp, sizeof(uint32_t) * kFrameWords) != cudaSuccess) return bail(V3DG_ECUDA);
+  if (cudaMallocHost(&c->h_tmp, sizeof(uint32_t) * (kFrameWords + 16)) != cudaSuccess) return bail(V3DG_ECUDA);
   std::memset(c->h_frame, 0, sizeof(uint32_t) * kFrameWords);
   if (dalloc(c, c->d_frame, sizeof(uint32_t) * kFrameWords, true) != V3DG_OK) return bail(V3DG_ENOMEM);
   if (dalloc(c, c->d_cutframe, sizeof(uint32_t) * kFrameWords, true) != V3DG_OK) return bail(V3DG_ENOMEM);
@@ -540,6 +546,7 @@ v3dg_status v3dg_set_option(v3dg_ctx* c, int option, int64_t value) {
   switch (option) {
     case V3DG_OPT_SYNC_CHECK: c->sync_check = value != 0; break;
     case V3DG_OPT_STAGE_TIMING: c->stage_timing = value != 0; break;
+    case V3DG_OPT_COUNT_WORK: c->count_work = value != 0; break;
     case V3DG_OPT_CAP_NODES:
       if (value < 64 || value > int64_t(kMaxNodes)) return fail(c, V3DG_EINVAL, "node capacity out of range");
       c->cap_nodes = uint32_t(value);
@@ -723,6 +730,7 @@ v3dg_status v3dg_frame_stats(v3dg_ctx* c, v3dg_stats* out) {
   out->pairs = f[kPairs];
   out->overflow = f[kOverflow];
   out->timeout = f[kTimeout];
+  if (c->count_work) std::memcpy(&out->blend_evals, c->h_tmp + kFrameWords, 2 * sizeof(unsigned long long));
   uint32_t ncut = 0, ng = 0;
   ST(run_cut(c, &ncut, &ng));
   out->cut_nodes = ncut;

@@ -88,9 +88,10 @@ cudaError_t launch_noderef(const uint2* render_list, uint32_t cap_nodes, const I
                            const uint32_t* frame, int sm_count, cudaStream_t st);
 
 // Records (3 float4 per slot, slot = render index * 64 + j):
-//   [0] = (u_rel, v_rel, na, nb), [1] = (nc, log2 o, r, g), [2] = (b, tile origin bits, 0, 0)
+//   [0] = (u_rel, v_rel, na, nb), [1] = (nc, log2 o, r, g), [2] = (b, tile origin, x range, y range)
 // with (u_rel, v_rel) the 2D mean relative to the pixel origin of the Gaussian's first tile
-// (tx0, ty0) and log2(alpha) = na dx^2 + nb dx dy + nc dy^2 + log2 o.
+// (tx0, ty0), log2(alpha) = na dx^2 + nb dx dy + nc dy^2 + log2 o, and the inclusive pixel
+// ranges x0 | x1 << 16, y0 | y1 << 16 of the alpha >= 1/255 ellipse's bounding box.
 cudaError_t launch_project(const uint2* render_list, uint32_t cap_nodes, const InstFrame* inst,
                            const AssetDev* assets, const CamConst& cam, const float4* ref, float4* rec,
                            uint2* rect, uint32_t* keys, uint32_t* frame, int sm_count, cudaStream_t st);
@@ -120,7 +121,8 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, const uint2* rect, co
                              uint32_t* pair_vals, uint32_t* frame, int sm_count, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const uint32_t* frame,
                           uint2* ranges, int n_tiles, int sm_count, cudaStream_t st);
+// work != nullptr: also count (evaluations, contributions) into work[0], work[1].
 cudaError_t launch_blend(const uint2* ranges, const uint32_t* pair_vals, const float4* rec, uint32_t cap_slots,
-                         const CamConst& cam, float* rgb, float* t_out, cudaStream_t st);
+                         const CamConst& cam, float* rgb, float* t_out, unsigned long long* work, cudaStream_t st);
 
 }  // namespace v3dg

@@ -37,7 +37,7 @@ def test_struct_sizes_match_the_header(native):
     import ctypes
     # v3dg_camera: 12 doubles + 4 floats + 2 int32 + float (+ padding to 8)
     assert ctypes.sizeof(native.v3dg_camera) == 96 + 16 + 8 + 4 + 4
-    assert ctypes.sizeof(native.v3dg_stats) == 5 * 8 + 2 * 4
+    assert ctypes.sizeof(native.v3dg_stats) == 5 * 8 + 2 * 4 + 2 * 8
 
 
 def test_no_gpu_means_an_error_not_a_fallback(native):

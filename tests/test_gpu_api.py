@@ -94,3 +94,22 @@ def test_launch_counter_and_stage_times(native, small_asset):
         ms, n1 = ctx.stage_times()
         assert n1 - n0 >= 10
         assert all(m >= 0 for m in ms) and sum(ms) > 0
+
+
+def test_work_counting_changes_nothing(native, small_asset):
+    from paper_2505_06523_gb300 import Context
+    cam = scenes.look_at((0.0, -2.6, 0.4), (0.0, 0.0, 0.0), 160, 120, 60.0)
+    with Context(0) as ctx:
+        ctx.load_hierarchy(small_asset)
+        ctx.set_instances(scenes.single_instance())
+        ctx.select(cam, 1.0)
+        a, _ = ctx.render()
+        a = a.cpu().numpy()
+        st0 = ctx.frame_stats()
+        ctx.set_option(native.V3DG_OPT_COUNT_WORK, 1)
+        ctx.select(cam, 1.0)
+        b, _ = ctx.render()
+        st = ctx.frame_stats()
+    assert (a == b.cpu().numpy()).all()
+    assert st0["blend_evals"] == 0
+    assert 0 < st["blend_contribs"] <= st["blend_evals"] <= st["pairs"] * 256
