@@ -232,34 +232,40 @@ def main():
     launches = ctx.launches() - n0
     per = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    stats = ctx.frame_stats()
+    stats = ctx.frame_stats()   # overflow / timeout flags are sticky over every timed frame
     if stats["overflow"] or stats["timeout"]:
-        raise RuntimeError(f"frame invalid during the timed region: {stats}")
+        raise RuntimeError(f"a frame of the timed region was invalid: {stats}")
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1000.0)
 
-    # per-stage device times (one extra timed frame with stage events) and the dominant kernel
-    ctx.set_option(N.V3DG_OPT_STAGE_TIMING, 1)
+    # per-stage device times over the same frames: replay them with stage events (synchronous, so
+    # the sum of the stages excludes the launch gaps that the asynchronous timed loop hides)
+    timed_ids = frame_ids[args.warmup:]
     ctx.set_option(N.V3DG_OPT_SYNC_CHECK, 1)
+    ctx.set_option(N.V3DG_OPT_STAGE_TIMING, 1)
     stage_runs = []
-    for s in range(5):
-        ctx.select(cams[frame_ids[s]], args.tau)
+    for fid in timed_ids:
+        ctx.select(cams[fid], args.tau)
         ctx.render(rgb)
         ms, _ = ctx.stage_times(len(STAGES))
         stage_runs.append(ms)
     ctx.set_option(N.V3DG_OPT_STAGE_TIMING, 0)
-    stage_ms = {k: float(np.median([r[i] for r in stage_runs])) for i, k in enumerate(STAGES)}
-    fs = ctx.frame_stats()
-    # the blend's work on the last of those frames (a separate, counting run of the same frame)
+    stage_ms = {k: float(np.mean([r[i] for r in stage_runs])) for i, k in enumerate(STAGES)}
+    # the blend's algorithmic work on the same frames (a separate, counting replay)
     ctx.set_option(N.V3DG_OPT_COUNT_WORK, 1)
-    ctx.select(cams[frame_ids[4]], args.tau)
-    ctx.render(rgb)
-    work = ctx.frame_stats()
+    frame_tot = {k: 0 for k in ("cut_nodes", "cut_gaussians", "render_nodes", "visible", "pairs", "blend_evals",
+                                "blend_contribs")}
+    for fid in timed_ids:
+        ctx.select(cams[fid], args.tau)
+        ctx.render(rgb)
+        st = ctx.frame_stats()
+        for k in frame_tot:
+            frame_tot[k] += st[k]
     ctx.set_option(N.V3DG_OPT_COUNT_WORK, 0)
-    fs["blend_evals"], fs["blend_contribs"] = work["blend_evals"], work["blend_contribs"]
+    fs = {k: v / len(timed_ids) for k, v in frame_tot.items()}
 
     # e2e through the public API with host buffers: per step, the instance table (host FP64) goes
     # in, the camera is set, and the RGB image comes back into pinned host memory
@@ -267,7 +273,7 @@ def main():
     e2e_steps = max(3, args.e2e_steps)
     for s in range(3):
         ctx.set_instances(inst)
-        ctx.select(cams[frame_ids[s]], args.tau)
+        ctx.select(cams[frame_ids[s % len(frame_ids)]], args.tau)
         ctx.render_host(host_rgb)
     t0 = time.perf_counter()
     for s in range(e2e_steps):
@@ -285,7 +291,7 @@ def main():
 
     peaks, peak_kind = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
-    roofline = roofline_for(dom, stage_ms, fs, peaks, peak_kind, stage_runs[-1])
+    roofline = roofline_for(dom, stage_ms, fs, peaks, peak_kind)
 
     line = None
     if rank == 0:
@@ -307,8 +313,8 @@ def main():
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "stages_ms": stage_ms,
-            "frame": {k: int(fs[k]) for k in ("cut_nodes", "cut_gaussians", "render_nodes", "visible", "pairs",
-                                              "blend_evals", "blend_contribs")},
+            "frame_mean": {k: int(round(v)) for k, v in fs.items()},
+            "stages_sum_ms": float(sum(stage_ms.values())),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
@@ -327,10 +333,11 @@ FP32_LANES = 152 * 128
 BLEND_OPS_EVAL, BLEND_OPS_CONTRIB = 8, 10
 
 
-def roofline_for(stage, stage_ms, fs, peaks, peak_kind, last_ms=None):
-    """Algorithmic work per launch of the dominant stage over its measured duration."""
+def roofline_for(stage, stage_ms, fs, peaks, peak_kind):
+    """Algorithmic work per launch of the dominant stage (means over the timed frames) over its
+    mean measured duration."""
     if stage == "blend" and fs.get("blend_evals"):
-        ms = last_ms[STAGES.index("blend")] if last_ms else stage_ms["blend"]
+        ms = stage_ms["blend"]
         ops = BLEND_OPS_EVAL * fs["blend_evals"] + BLEND_OPS_CONTRIB * fs["blend_contribs"]
         mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak = FP32_LANES * mhz * 1e6 / 1e12

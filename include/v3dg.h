@@ -93,8 +93,9 @@ typedef struct {
   uint64_t render_nodes;    /* cut clusters left after the conservative visibility cull */
   uint64_t visible;         /* Gaussians that survive the projection culls */
   uint64_t pairs;           /* (tile, Gaussian) pairs sorted and blended */
-  uint32_t overflow;        /* nonzero if a capacity was exceeded (outputs invalid) */
-  uint32_t timeout;         /* nonzero if a bounded device wait gave up (outputs invalid) */
+  uint32_t overflow;        /* nonzero if a capacity was exceeded in the last frame, or in any
+                               frame rendered since the previous v3dg_frame_stats call */
+  uint32_t timeout;         /* likewise for a bounded device wait that gave up */
   uint64_t blend_evals;     /* (pixel, Gaussian) pairs the blend evaluated inside the Gaussian's
                                pixel box (only with V3DG_OPT_COUNT_WORK, else 0) */
   uint64_t blend_contribs;  /* of those, the ones with alpha >= 1/255 that were blended */

@@ -14,37 +14,26 @@ namespace {
 constexpr int kBins = 256;
 constexpr int kWarps = kSortThreads / 32;
 
-// Digit counts of every pass in one read of the keys.  Keys are often concentrated in a few
-// digits (the high bytes of float depths), so equal digits within a warp are combined first
-// (match + popc) and counted with one shared atomic, into per-warp sub-histograms.
+// Digit counts of every pass in one read of the keys (one shared histogram per pass and block).
 __global__ void __launch_bounds__(256)
 k_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev, uint32_t cap, int begin_bit,
        int end_bit, int passes, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t sh[8][4][kBins];
-  const int warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < 8 * 4 * kBins; i += blockDim.x) (&sh[0][0][0])[i] = 0;
+  __shared__ uint32_t sh[4][kBins];
+  for (int i = threadIdx.x; i < 4 * kBins; i += blockDim.x) sh[i / kBins][i % kBins] = 0;
   __syncthreads();
   const uint32_t n = min(*n_dev, cap);
   const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t n_round = (n + 31u) & ~31u;   // whole warps iterate together
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-    const bool ok = i < n;
-    const uint32_t k = ok ? keys[i] : 0u;
-    const uint32_t live = __ballot_sync(0xffffffffu, ok);
-    if (!ok) continue;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t k = keys[i];
     for (int p = 0; p < passes; ++p) {
       const int sh_ = begin_bit + 8 * p;
       const uint32_t m = end_bit - sh_ >= 8 ? 0xFFu : ((1u << (end_bit - sh_)) - 1u);
-      const uint32_t d = (k >> sh_) & m;
-      const uint32_t peers = __match_any_sync(live, d);
-      if ((peers & lanemask_lt()) == 0) atomicAdd(&sh[warp][p][d], __popc(peers));
+      atomicAdd(&sh[p][(k >> sh_) & m], 1u);
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * kBins; i += blockDim.x) {
-    uint32_t c = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) c += sh[w][i / kBins][i % kBins];
+    const uint32_t c = sh[i / kBins][i % kBins];
     if (c) atomicAdd(hist + i, c);
   }
 }
@@ -65,12 +54,13 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-  for (int i = tid; i < kWarps * kBins; i += kSortThreads) (&s_wh[0][0])[i] = 0;
   __syncthreads();
   const uint32_t n = min(*n_dev, cap);
   const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
   const uint32_t tile = s_tile;
-  if (tile >= ntiles) return;
+  if (tile >= ntiles) return;  // the grid is sized by capacity: surplus blocks leave at once
+  for (int i = tid; i < kWarps * kBins; i += kSortThreads) (&s_wh[0][0])[i] = 0;
+  __syncthreads();
   const uint32_t base = tile * kSortTile + warp * (kSortItems * 32);
 
   uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];

@@ -366,7 +366,9 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
   // d_misc: [0..7] the standalone sort's words, [8..11] two 64-bit blend work counters
   unsigned long long* work = c->count_work ? reinterpret_cast<unsigned long long*>(P<uint32_t>(c->d_misc) + 8) : nullptr;
   if (work) CU(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), c->stream));
-  CU(launch_blend(P<uint2>(c->d_ranges), tv, P<float4>(c->d_rec), c->cap_slots, k, rgb, t_out, work, c->stream));
+  // d_misc[12], [13]: sticky overflow / timeout flags of all frames since the last v3dg_frame_stats
+  CU(launch_blend(P<uint2>(c->d_ranges), tv, P<float4>(c->d_rec), c->cap_slots, k, rgb, t_out, work, frame,
+                  P<uint32_t>(c->d_misc) + 12, c->stream));
   c->launches += 1;
   if (work)
     CU(cudaMemcpyAsync(c->h_tmp + kFrameWords, work, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
@@ -397,6 +399,8 @@ v3dg_status run_frame(v3dg_ctx* c, float* rgb, float* t_out) {
       if (want > kMaxPairs) return fail(c, V3DG_EOVERFLOW, "%u pairs exceed the limit", f[kPairs]);
       c->cap_pairs = uint32_t(want);
     }
+    // the frame is re-run: its overflow must not linger in the sticky flags
+    CU(cudaMemsetAsync(P<uint32_t>(c->d_misc) + 12, 0, 2 * sizeof(uint32_t), c->stream));
     ST(enqueue_select(c));
   }
   return fail(c, V3DG_EOVERFLOW, "frame still overflows after growing the buffers");
@@ -728,8 +732,11 @@ v3dg_status v3dg_frame_stats(v3dg_ctx* c, v3dg_stats* out) {
   out->render_nodes = f[kRenderNodes];
   out->visible = f[kVisible];
   out->pairs = f[kPairs];
-  out->overflow = f[kOverflow];
-  out->timeout = f[kTimeout];
+  uint32_t sticky[2] = {0, 0};
+  CU(cudaMemcpy(sticky, P<uint32_t>(c->d_misc) + 12, sizeof sticky, cudaMemcpyDeviceToHost));
+  CU(cudaMemset(P<uint32_t>(c->d_misc) + 12, 0, sizeof sticky));
+  out->overflow = f[kOverflow] | sticky[0];
+  out->timeout = f[kTimeout] | sticky[1];
   if (c->count_work) std::memcpy(&out->blend_evals, c->h_tmp + kFrameWords, 2 * sizeof(unsigned long long));
   uint32_t ncut = 0, ng = 0;
   ST(run_cut(c, &ncut, &ng));

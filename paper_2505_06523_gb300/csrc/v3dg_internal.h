@@ -122,7 +122,10 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, const uint2* rect, co
 cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const uint32_t* frame,
                           uint2* ranges, int n_tiles, int sm_count, cudaStream_t st);
 // work != nullptr: also count (evaluations, contributions) into work[0], work[1].
+// sticky[0] |= frame[kOverflow], sticky[1] |= frame[kTimeout] (the flags of every frame since the
+// host last cleared them).
 cudaError_t launch_blend(const uint2* ranges, const uint32_t* pair_vals, const float4* rec, uint32_t cap_slots,
-                         const CamConst& cam, float* rgb, float* t_out, unsigned long long* work, cudaStream_t st);
+                         const CamConst& cam, float* rgb, float* t_out, unsigned long long* work,
+                         const uint32_t* frame, uint32_t* sticky, cudaStream_t st);
 
 }  // namespace v3dg
