@@ -7,14 +7,17 @@
 
 namespace v3dg {
 
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+// A status word carries its flag and its value in one aligned 64-bit word, so a reader that sees
+// the flag sees the value with it: relaxed (uncached, single-copy atomic) accesses suffice and no
+// fence is needed.
+__device__ __forceinline__ uint64_t ld_status(const uint64_t* p) {
   uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_status(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ uint64_t pack_status(uint32_t epoch, uint64_t flag, uint32_t value) {
@@ -29,15 +32,15 @@ __device__ __forceinline__ uint64_t pack_status(uint32_t epoch, uint64_t flag, u
 __device__ __forceinline__ uint32_t chained_exclusive(uint64_t* status, uint32_t stride, uint32_t tile,
                                                       uint32_t agg, uint32_t epoch, uint32_t* err) {
   if (tile == 0) {
-    st_release(status, pack_status(epoch, kFlagPrefix, agg));
+    st_status(status, pack_status(epoch, kFlagPrefix, agg));
     return 0;
   }
-  st_release(status + size_t(tile) * stride, pack_status(epoch, kFlagAgg, agg));
+  st_status(status + size_t(tile) * stride, pack_status(epoch, kFlagAgg, agg));
   uint32_t excl = 0;
   int64_t j = int64_t(tile) - 1;
   uint32_t spins = 0;
   while (j >= 0) {
-    const uint64_t s = ld_acquire(status + size_t(j) * stride);
+    const uint64_t s = ld_status(status + size_t(j) * stride);
     const uint32_t flag = uint32_t(s >> 32) & 3u;
     if (uint32_t(s >> 34) != epoch || flag == 0) {
       if (++spins > kSpinLimit) {
@@ -51,7 +54,7 @@ __device__ __forceinline__ uint32_t chained_exclusive(uint64_t* status, uint32_t
     if (flag == kFlagPrefix) break;
     --j;
   }
-  st_release(status + size_t(tile) * stride, pack_status(epoch, kFlagPrefix, excl + agg));
+  st_status(status + size_t(tile) * stride, pack_status(epoch, kFlagPrefix, excl + agg));
   return excl;
 }
 

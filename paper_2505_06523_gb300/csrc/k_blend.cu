@@ -12,6 +12,11 @@
 // gives the record's row and column masks in this tile and the set of warp blocks it touches;
 // ballots turn the latter into one bit list per warp, so a warp visits only the records that
 // reach its pixels, still in depth order, and stops as soon as all its pixels are done.
+// Tiles differ in cost by orders of magnitude (long lists of tiny distant Gaussians rarely
+// saturate a pixel), so the grid is persistent and blocks take tiles heaviest-first: k_tile_order
+// buckets the tiles by log2 of their pair count, and blocks pull the next tile of that order.
+#include <algorithm>
+
 #include "dev_common.cuh"
 
 namespace v3dg {
@@ -21,10 +26,39 @@ constexpr int kBlendThreads = 256;
 constexpr int kBlendWarps = kBlendThreads / 32;
 constexpr float kLog2MinAlpha = -7.9943534f;  // log2(1/255)
 
+// Tile order, heaviest first: one block buckets the tiles by floor(log2(pairs + 1)) (descending).
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, int n_tiles,
+                                                     uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_hist[32];
+  if (threadIdx.x < 32) s_hist[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+    const uint2 r = ranges[t];
+    atomicAdd(&s_hist[__clz(r.y - r.x + 1u)], 1u);   // clz: 0 for the heaviest bucket
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const uint32_t v = s_hist[threadIdx.x];
+    uint32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (threadIdx.x >= d) incl += t;
+    }
+    s_hist[threadIdx.x] = incl - v;   // cursor: first position of the bucket
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+    const uint2 r = ranges[t];
+    order[atomicAdd(&s_hist[__clz(r.y - r.x + 1u)], 1u)] = uint32_t(t);
+  }
+}
+
 template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads)
-k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv, const float4* __restrict__ rec,
-        uint32_t cap_slots, int width, int height, int tiles_x, float* __restrict__ rgb, float* __restrict__ t_out,
+k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, uint32_t* __restrict__ tile_counter,
+        int n_tiles, const uint32_t* __restrict__ pv, const float4* __restrict__ rec, uint32_t cap_slots, int width,
+        int height, int tiles_x, float* __restrict__ rgb, float* __restrict__ t_out,
         unsigned long long* __restrict__ work, const uint32_t* __restrict__ frame, uint32_t* __restrict__ sticky) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (frame[kOverflow]) atomicOr(sticky, 1u);
@@ -34,18 +68,25 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv, const
   __shared__ float4 s_c[kBlendThreads];             // (nc, log2 o, r, g)
   __shared__ float2 s_b[kBlendThreads];             // (b, row mask << 16 | column mask)
   __shared__ uint32_t s_list[kBlendWarps][kBlendWarps];  // [warp block][staging warp]: record bits
-  const int tile = blockIdx.x;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  __shared__ uint32_t s_next;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = 8 * (warp & 1) + (lane & 7), ly = 4 * (warp >> 1) + (lane >> 3);
-  const int px = tx * 16 + lx, py = ty * 16 + ly;
-  const bool inside = px < width && py < height;
   const float fx = float(lx) + 0.5f, fy = float(ly) + 0.5f;
   const uint32_t mybits = (1u << lx) | (1u << (16 + ly));
+  uint32_t n_eval = 0, n_contrib = 0;
+  for (;;) {
+  if (threadIdx.x == 0) s_next = atomicAdd(tile_counter, 1u);
+  __syncthreads();
+  const uint32_t next = s_next;
+  __syncthreads();
+  if (next >= uint32_t(n_tiles)) break;
+  const int tile = int(order[next]);
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  const int px = tx * 16 + lx, py = ty * 16 + ly;
+  const bool inside = px < width && py < height;
   const uint2 range = ranges[tile];
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
   bool done = !inside;
-  uint32_t n_eval = 0, n_contrib = 0;
   for (uint32_t b0 = range.x; b0 < range.y; b0 += kBlendThreads) {
     if (__syncthreads_count(done) == kBlendThreads) break;
     const uint32_t i = b0 + threadIdx.x;
@@ -124,6 +165,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv, const
     rgb[3 * p + 2] = cb;
     if (t_out) t_out[p] = T;
   }
+  }  // next tile
   if (kCount) {
     unsigned long long e = n_eval, cnt = n_contrib;
 #pragma unroll
@@ -140,17 +182,20 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv, const
 
 }  // namespace
 
-cudaError_t launch_blend(const uint2* ranges, const uint32_t* pv, const float4* rec, uint32_t cap_slots,
-                         const CamConst& cam, float* rgb, float* t_out, unsigned long long* work,
-                         const uint32_t* frame, uint32_t* sticky, cudaStream_t st) {
+cudaError_t launch_blend(const uint2* ranges, uint32_t* order, uint32_t* tile_counter, const uint32_t* pv,
+                         const float4* rec, uint32_t cap_slots, const CamConst& cam, float* rgb, float* t_out,
+                         unsigned long long* work, const uint32_t* frame, uint32_t* sticky, int sm_count,
+                         cudaStream_t st) {
   const int n_tiles = cam.tiles_x * cam.tiles_y;
   if (n_tiles == 0) return cudaSuccess;
+  k_tile_order<<<1, 1024, 0, st>>>(ranges, n_tiles, order);
+  const int grid = std::min(n_tiles, sm_count * 6);
   if (work)
-    k_blend<true><<<n_tiles, kBlendThreads, 0, st>>>(ranges, pv, rec, cap_slots, cam.width, cam.height, cam.tiles_x,
-                                                     rgb, t_out, work, frame, sticky);
+    k_blend<true><<<grid, kBlendThreads, 0, st>>>(ranges, order, tile_counter, n_tiles, pv, rec, cap_slots, cam.width,
+                                                  cam.height, cam.tiles_x, rgb, t_out, work, frame, sticky);
   else
-    k_blend<false><<<n_tiles, kBlendThreads, 0, st>>>(ranges, pv, rec, cap_slots, cam.width, cam.height, cam.tiles_x,
-                                                      rgb, t_out, nullptr, frame, sticky);
+    k_blend<false><<<grid, kBlendThreads, 0, st>>>(ranges, order, tile_counter, n_tiles, pv, rec, cap_slots, cam.width,
+                                                   cam.height, cam.tiles_x, rgb, t_out, nullptr, frame, sticky);
   return cudaGetLastError();
 }
 

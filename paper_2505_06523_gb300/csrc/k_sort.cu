@@ -13,6 +13,7 @@ namespace {
 
 constexpr int kBins = 256;
 constexpr int kWarps = kSortThreads / 32;
+static_assert(kSortThreads >= kBins, "one thread per digit");
 
 // Digit counts of every pass in one read of the keys (one shared histogram per pass and block).
 __global__ void __launch_bounds__(256)
@@ -38,15 +39,26 @@ k_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev, ui
   }
 }
 
+// Exclusive scan over digits of each pass's global histogram: the first output position of each
+// digit (one block, one thread per digit).
+__global__ void __launch_bounds__(kBins) k_hist_scan(const uint32_t* __restrict__ hist, int passes,
+                                                     uint32_t* __restrict__ excl) {
+  __shared__ uint32_t s_scan[kBins / 32 + 1];
+  for (int p = 0; p < passes; ++p) {
+    uint32_t total;
+    excl[p * kBins + threadIdx.x] = block_exclusive_scan<kBins / 32>(hist[p * kBins + threadIdx.x], s_scan, &total);
+  }
+}
+
 template <bool kImplicit>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 3)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
            uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev, uint32_t cap, int shift, uint32_t dmask,
-           const uint32_t* __restrict__ ghist, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
+           const uint32_t* __restrict__ gexcl, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
            uint32_t epoch, uint32_t* __restrict__ err) {
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
-  __shared__ uint32_t s_wh[kWarps][kBins];   // per-warp digit counts, then per-warp exclusive offsets
+  __shared__ uint16_t s_wh[kWarps][kBins];   // per-warp digit counts, then per-warp exclusive offsets
   __shared__ uint32_t s_start[kBins];        // block-local start of each digit
   __shared__ int32_t s_goff[kBins];          // global destination offset minus local start
   __shared__ uint32_t s_scan[kWarps + 1];
@@ -59,7 +71,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
   const uint32_t tile = s_tile;
   if (tile >= ntiles) return;  // the grid is sized by capacity: surplus blocks leave at once
-  for (int i = tid; i < kWarps * kBins; i += kSortThreads) (&s_wh[0][0])[i] = 0;
+  for (int i = tid; i < kWarps * kBins / 2; i += kSortThreads) reinterpret_cast<uint32_t*>(&s_wh[0][0])[i] = 0;
   __syncthreads();
   const uint32_t base = tile * kSortTile + warp * (kSortItems * 32);
 
@@ -71,7 +83,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     key[i] = ok ? kin[idx] : 0xFFFFFFFFu;
     val[i] = kImplicit ? idx : (ok ? vin[idx] : 0u);
   }
-  // warp-level stable ranking
+  // warp-level stable ranking: item-major, then lane order
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t idx = base + i * 32 + lane;
@@ -84,27 +96,29 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
       const uint32_t before = __popc(peers & lanemask_lt());
       const uint32_t cur = s_wh[warp][d];
       __syncwarp(live);
-      if (before == 0) s_wh[warp][d] = cur + __popc(peers);
+      if (before == 0) s_wh[warp][d] = uint16_t(cur + __popc(peers));
       __syncwarp(live);
       rank[i] = cur + before;
     }
   }
   __syncthreads();
-  // per digit: exclusive offsets across warps and the block count
-  const uint32_t d = tid;  // kSortThreads == kBins
+  // per digit (threads 0..255): exclusive offsets across warps, the block count, and the chain
   uint32_t cnt = 0;
+  if (tid < kBins) {
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    const uint32_t c = s_wh[w][d];
-    s_wh[w][d] = cnt;
-    cnt += c;
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = s_wh[w][tid];
+      s_wh[w][tid] = uint16_t(cnt);
+      cnt += c;
+    }
   }
   uint32_t total;
   const uint32_t start = block_exclusive_scan<kWarps>(cnt, s_scan, &total);
-  const uint32_t gstart = block_exclusive_scan<kWarps>(ghist[d], s_scan, &total);
-  s_start[d] = start;
-  const uint32_t excl = chained_exclusive(status + d, kBins, tile, cnt, epoch, err);
-  s_goff[d] = int32_t(gstart + excl) - int32_t(start);
+  if (tid < kBins) {
+    s_start[tid] = start;
+    const uint32_t excl = chained_exclusive(status + tid, kBins, tile, cnt, epoch, err);
+    s_goff[tid] = int32_t(gexcl[tid] + excl) - int32_t(start);
+  }
   __syncthreads();
   // reorder the tile by digit in shared memory
 #pragma unroll
@@ -143,7 +157,14 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
   cudaError_t e = cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * kBins * passes, st);
   if (e != cudaSuccess) return e;
   k_hist<<<sm_count * 4, 256, 0, st>>>(k0, n_dev, cap, begin_bit, end_bit, passes, sc.hist);
-  ++*launches;
+  k_hist_scan<<<1, kBins, 0, st>>>(sc.hist, passes, sc.hist + 4 * kBins);
+  *launches += 2;
+  static bool carveout_set = false;
+  if (!carveout_set) {
+    cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    carveout_set = true;
+  }
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int p = 0; p < passes; ++p) {
     const int shift = begin_bit + 8 * p;
@@ -152,10 +173,10 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
     if (epoch == 0) epoch = 1;
     const uint32_t ep = epoch;
     if (p == 0 && implicit_vals)
-      k_onesweep<true><<<max_tiles, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + kBins * p,
+      k_onesweep<true><<<max_tiles, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + 4 * kBins + kBins * p,
                                                            sc.status, sc.tile_counters + p, ep, err_flag);
     else
-      k_onesweep<false><<<max_tiles, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + kBins * p,
+      k_onesweep<false><<<max_tiles, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + 4 * kBins + kBins * p,
                                                             sc.status, sc.tile_counters + p, ep, err_flag);
     ++*launches;
     e = cudaGetLastError();

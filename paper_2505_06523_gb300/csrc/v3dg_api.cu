@@ -72,7 +72,7 @@ struct v3dg_ctx {
   uint32_t cap_nodes = 0, cap_slots = 0, cap_pairs = 0, status_words = 0, cap_cut = 0;
   DevBuf d_list, d_ref, d_keys0, d_keys1, d_vals0, d_vals1, d_rec, d_rect, d_off;
   DevBuf d_pk0, d_pk1, d_pv0, d_pv1, d_ranges, d_status, d_hist, d_cut;
-  DevBuf d_img, d_timg, d_sort_k, d_sort_v;
+  DevBuf d_img, d_timg, d_sort_k, d_sort_v, d_order;
   bool depth_in1 = false, tiles_in1 = false;
   uint32_t epoch = 1;
   uint64_t launches = 0;
@@ -191,7 +191,7 @@ v3dg_status ensure_work(v3dg_ctx* c) {
   words = std::max<uint64_t>(words, uint64_t(c->n_inst_frame) * uint64_t(std::max(c->node_blocks, 1)));
   words = std::max<uint64_t>(words, (uint64_t(S) + 1023) / 1024);
   ST(ensure_status(c, words));
-  ST(ensure(c, c->d_hist, 4 * 256 * 4));
+  ST(ensure(c, c->d_hist, 2 * 4 * 256 * 4));  // counts + exclusive offsets of up to 4 passes
   return V3DG_OK;
 }
 
@@ -304,8 +304,12 @@ v3dg_status enqueue_select(v3dg_ctx* c) {
   return V3DG_OK;
 }
 
-__global__ void k_slot_count(uint32_t* frame, uint32_t cap_nodes) {
-  frame[kSlotCount] = min(frame[kRenderNodes], cap_nodes) * uint32_t(kSlots);
+// Start of a render: zero the render stages' counters (select's words stay, so that a render
+// list overflow still invalidates the frame) and count the slots the depth sort covers.
+__global__ void k_render_reset(uint32_t* frame, uint32_t cap_nodes) {
+  const int i = threadIdx.x;
+  if (i == kVisible || i == kPairs || i == kPairsEff || (i > kTileCounters && i < kFrameWords)) frame[i] = 0;
+  if (i == kSlotCount) frame[kSlotCount] = min(frame[kRenderNodes], cap_nodes) * uint32_t(kSlots);
 }
 
 __global__ void k_set_word(uint32_t* p, uint32_t v) { *p = v; }
@@ -315,7 +319,7 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
   uint32_t* frame = P<uint32_t>(c->d_frame);
   const int sm = c->sm_count;
   stage_event(c, kStageProject);
-  k_slot_count<<<1, 1, 0, c->stream>>>(frame, c->cap_nodes);
+  k_render_reset<<<1, kFrameWords, 0, c->stream>>>(frame, c->cap_nodes);
   CU(cudaGetLastError());
   CU(launch_noderef(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->d_assets), k,
                     P<float4>(c->d_ref), frame, sm, c->stream));
@@ -359,6 +363,7 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
 
   stage_event(c, kStageRanges);
   ST(ensure(c, c->d_ranges, sizeof(uint2) * size_t(n_tiles)));
+  ST(ensure(c, c->d_order, sizeof(uint32_t) * size_t(n_tiles)));
   CU(launch_ranges(tk, c->cap_pairs, frame, P<uint2>(c->d_ranges), n_tiles, sm, c->stream));
   c->launches += 1;
 
@@ -367,9 +372,9 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
   unsigned long long* work = c->count_work ? reinterpret_cast<unsigned long long*>(P<uint32_t>(c->d_misc) + 8) : nullptr;
   if (work) CU(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), c->stream));
   // d_misc[12], [13]: sticky overflow / timeout flags of all frames since the last v3dg_frame_stats
-  CU(launch_blend(P<uint2>(c->d_ranges), tv, P<float4>(c->d_rec), c->cap_slots, k, rgb, t_out, work, frame,
-                  P<uint32_t>(c->d_misc) + 12, c->stream));
-  c->launches += 1;
+  CU(launch_blend(P<uint2>(c->d_ranges), P<uint32_t>(c->d_order), frame + kTileCounters + 10, tv, P<float4>(c->d_rec),
+                  c->cap_slots, k, rgb, t_out, work, frame, P<uint32_t>(c->d_misc) + 12, sm, c->stream));
+  c->launches += 2;
   if (work)
     CU(cudaMemcpyAsync(c->h_tmp + kFrameWords, work, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   stage_event(c, kStages);
@@ -525,7 +530,7 @@ void v3dg_destroy(v3dg_ctx* c) {
   DevBuf* bs[] = {&c->d_assets, &c->d_inst, &c->d_frame, &c->d_cutframe, &c->d_misc, &c->d_list, &c->d_ref,
                   &c->d_keys0, &c->d_keys1, &c->d_vals0, &c->d_vals1, &c->d_rec, &c->d_rect, &c->d_off, &c->d_pk0,
                   &c->d_pk1, &c->d_pv0, &c->d_pv1, &c->d_ranges, &c->d_status, &c->d_hist, &c->d_cut, &c->d_img,
-                  &c->d_timg, &c->d_sort_k, &c->d_sort_v};
+                  &c->d_timg, &c->d_sort_k, &c->d_sort_v, &c->d_order};
   for (DevBuf* b : bs) dfree(c, *b);
   if (c->h_inst) cudaFreeHost(c->h_inst);
   if (c->h_frame) cudaFreeHost(c->h_frame);
@@ -894,7 +899,7 @@ v3dg_status v3dg_sort_pairs(v3dg_ctx* c, uint32_t* keys, uint32_t* vals, uint64_
   ST(ensure(c, c->d_sort_k, 4 * n));
   ST(ensure(c, c->d_sort_v, 4 * n));
   ST(ensure_status(c, ((n + kSortTile - 1) / kSortTile) * 256));
-  ST(ensure(c, c->d_hist, 4 * 256 * 4));
+  ST(ensure(c, c->d_hist, 2 * 4 * 256 * 4));  // counts + exclusive offsets of up to 4 passes
   uint32_t* misc = P<uint32_t>(c->d_misc);  // [0] n, [1..4] tile counters, [5] timeout flag
   CU(cudaMemsetAsync(misc, 0, sizeof(uint32_t) * 8, c->stream));
   k_set_word<<<1, 1, 0, c->stream>>>(misc, uint32_t(n));

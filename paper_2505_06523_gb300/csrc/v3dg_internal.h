@@ -101,12 +101,12 @@ cudaError_t launch_project(const uint2* render_list, uint32_t cap_nodes, const I
 // (k1, v1) -- *result_in_1 tells which.  implicit_vals: the values of the first pass are the
 // element indices (v0 is not read).
 struct SortScratch {
-  uint32_t* hist;          // 4 passes * 256
+  uint32_t* hist;          // 4 passes * 256 counts, then 4 passes * 256 exclusive offsets
   uint64_t* status;        // max_tiles * 256
   uint32_t max_tiles;
   uint32_t* tile_counters; // one per pass (zeroed by the caller's frame memset)
 };
-constexpr int kSortThreads = 256, kSortItems = 16, kSortTile = kSortThreads * kSortItems;
+constexpr int kSortThreads = 512, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
 cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
                         uint32_t cap, int begin_bit, int end_bit, bool implicit_vals,
                         const SortScratch& sc, uint32_t* err_flag, uint32_t& epoch, int sm_count,
@@ -124,8 +124,10 @@ cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const u
 // work != nullptr: also count (evaluations, contributions) into work[0], work[1].
 // sticky[0] |= frame[kOverflow], sticky[1] |= frame[kTimeout] (the flags of every frame since the
 // host last cleared them).
-cudaError_t launch_blend(const uint2* ranges, const uint32_t* pair_vals, const float4* rec, uint32_t cap_slots,
-                         const CamConst& cam, float* rgb, float* t_out, unsigned long long* work,
-                         const uint32_t* frame, uint32_t* sticky, cudaStream_t st);
+// order: n_tiles words of scratch (the heaviest-first tile order); tile_counter: a zeroed word.
+cudaError_t launch_blend(const uint2* ranges, uint32_t* order, uint32_t* tile_counter, const uint32_t* pair_vals,
+                         const float4* rec, uint32_t cap_slots, const CamConst& cam, float* rgb, float* t_out,
+                         unsigned long long* work, const uint32_t* frame, uint32_t* sticky, int sm_count,
+                         cudaStream_t st);
 
 }  // namespace v3dg

@@ -31,7 +31,7 @@ constexpr size_t kOffKeys = 0;
 constexpr size_t kOffVals = kOffKeys + 4 * kMaxPairs;
 constexpr size_t kOffStatus = kOffVals + 4 * kMaxPairs;
 constexpr size_t kOffHist = kOffStatus + 8 * size_t(kTiles) * 256;
-constexpr size_t kOffMisc = kOffHist + 4 * 256 * 4;   // [0] n, [1..4] tile counters, [5] timeout flag
+constexpr size_t kOffMisc = kOffHist + 2 * 4 * 256 * 4;   // [0] n, [1..4] tile counters, [5] timeout flag
 constexpr size_t kBytes = kOffMisc + 256;
 constexpr int kMaxDevices = 64;
 

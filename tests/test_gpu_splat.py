@@ -168,3 +168,18 @@ def test_deterministic_repeat(Context, tiny_asset, small_asset):
     b = _frame(Context, [tiny_asset, small_asset], inst, cam, 1.0)
     assert (a["rgb"] == b["rgb"]).all()
     assert all((a["pairs"][k] == b["pairs"][k]).all() for k in a["pairs"])
+
+
+def test_render_twice_after_one_select(Context, small_asset):
+    """Every render recomputes the frame: a second render after one select gives the same image."""
+    cam = scenes.look_at((0.3, -2.4, 0.5), (0.0, 0.0, 0.0), 128, 96, 60.0)
+    with Context(0) as ctx:
+        ctx.load_hierarchy(small_asset)
+        ctx.set_instances(scenes.single_instance())
+        ctx.select(cam, 1.0)
+        a, _ = ctx.render()
+        a = a.clone()
+        b = ctx.render()[0]
+        c = ctx.render()[0]
+    assert float(a.abs().sum()) > 0
+    assert (a == b).all() and (a == c).all()
