@@ -1,4 +1,4 @@
-// Tile binning: pair offsets, duplication of each visible Gaussian into its tiles, tile ranges.
+// Tile binning: expansion of each visible Gaussian into its (tile, Gaussian) pairs, tile ranges.
 //
 // The Gaussians arrive sorted by depth (stage one of the two-stage (tile, depth) sort), so the
 // pairs are emitted in depth order; a stable sort on the tile id then yields (tile, depth, id)
@@ -8,66 +8,82 @@
 namespace v3dg {
 namespace {
 
-constexpr int kScanThreads = 256, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
-
 __device__ __forceinline__ uint32_t rect_area(const uint2 r) {
   const uint32_t w = (r.x >> 16) - (r.x & 0xFFFFu) + 1u;
   const uint32_t h = (r.y >> 16) - (r.y & 0xFFFFu) + 1u;
   return w * h;
 }
 
-__global__ void __launch_bounds__(kScanThreads)
-k_pair_scan(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uint32_t cap,
-            uint32_t* __restrict__ offsets, uint32_t* __restrict__ frame, uint32_t tc_slot,
-            uint64_t* __restrict__ status, uint32_t epoch) {
-  __shared__ uint32_t s_tile, s_excl;
-  __shared__ uint32_t s_scan[kScanThreads / 32 + 1];
+constexpr int kExpThreads = 256, kExpItems = 4, kExpTile = kExpThreads * kExpItems;
+
+// One pass over the depth-sorted visible Gaussians: each block takes 1024 of them, scans their
+// tile counts, finds its first pair position with a bounded look-back and then writes its pairs
+// cooperatively: output position p belongs to the Gaussian j with off[j] <= p < off[j + 1]
+// (binary search in shared memory), so large Gaussians are spread over the whole block and the
+// writes are contiguous.
+__global__ void __launch_bounds__(kExpThreads)
+k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uint32_t cap, uint32_t cap_pairs,
+         int tiles_x, uint32_t* __restrict__ pk, uint32_t* __restrict__ pv, uint32_t* __restrict__ frame,
+         uint32_t tc_slot, uint64_t* __restrict__ status, uint32_t epoch) {
+  __shared__ uint32_t s_off[kExpTile + 1];
+  __shared__ uint2 s_rect[kExpTile];
+  __shared__ uint32_t s_slot[kExpTile];
+  __shared__ uint32_t s_scan[kExpThreads / 32 + 1];
+  __shared__ uint32_t s_tile, s_base;
   if (threadIdx.x == 0) s_tile = atomicAdd(frame + kTileCounters + tc_slot, 1u);
   __syncthreads();
   const uint32_t n = min(frame[kVisible], cap);
-  const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+  const uint32_t ntiles = (n + kExpTile - 1) / kExpTile;
   const uint32_t tile = s_tile;
   if (tile >= ntiles) return;
-  const uint32_t i0 = tile * kScanTile + threadIdx.x * kScanItems;
-  uint32_t c[kScanItems], sum = 0;
+  const uint32_t first = tile * kExpTile;
+  const uint32_t items = min(uint32_t(kExpTile), n - first);
+  uint32_t c[kExpItems], sum = 0;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    c[i] = (i0 + i < n) ? rect_area(rect[slots[i0 + i]]) : 0u;
+  for (int i = 0; i < kExpItems; ++i) {
+    const uint32_t j = threadIdx.x * kExpItems + i;
+    c[i] = 0;
+    if (j < items) {
+      const uint32_t slot = slots[first + j];
+      const uint2 r = rect[slot];
+      s_slot[j] = slot;
+      s_rect[j] = r;
+      c[i] = rect_area(r);
+    }
     sum += c[i];
   }
   uint32_t total;
-  uint32_t ex = block_exclusive_scan<kScanThreads / 32>(sum, s_scan, &total);
-  if (threadIdx.x == 0) s_excl = chained_exclusive(status, 1, tile, total, epoch, frame + kTimeout);
-  __syncthreads();
-  ex += s_excl;
+  uint32_t ex = block_exclusive_scan<kExpThreads / 32>(sum, s_scan, &total);
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    if (i0 + i < n) offsets[i0 + i] = ex;
+  for (int i = 0; i < kExpItems; ++i) {
+    s_off[threadIdx.x * kExpItems + i] = ex;
     ex += c[i];
   }
-  if (threadIdx.x == 0 && tile == ntiles - 1) frame[kPairs] = s_excl + total;
-}
-
-__global__ void __launch_bounds__(256)
-k_duplicate(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, const uint32_t* __restrict__ offsets,
-            uint32_t cap, uint32_t cap_pairs, int tiles_x, uint32_t* __restrict__ pk, uint32_t* __restrict__ pv,
-            uint32_t* __restrict__ frame) {
-  const uint32_t n = min(frame[kVisible], cap);
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const uint32_t slot = slots[k];
-    const uint2 r = rect[slot];
-    const uint32_t tx0 = r.x & 0xFFFFu, tx1 = r.x >> 16, ty0 = r.y & 0xFFFFu, ty1 = r.y >> 16;
-    uint32_t o = offsets[k];
-    if (uint64_t(o) + rect_area(r) > cap_pairs) {
-      atomicOr(frame + kOverflow, 1u);
-      continue;
+  if (threadIdx.x == 0) {
+    s_off[kExpTile] = total;
+    s_base = chained_exclusive(status, 1, tile, total, epoch, frame + kTimeout);
+    if (tile == ntiles - 1) frame[kPairs] = s_base + total;
+  }
+  __syncthreads();
+  const uint32_t base = s_base;
+  if (uint64_t(base) + total > cap_pairs) {
+    if (threadIdx.x == 0) atomicOr(frame + kOverflow, 1u);
+    return;
+  }
+  for (uint32_t p = threadIdx.x; p < total; p += kExpThreads) {
+    // last item j < items with s_off[j] <= p
+    uint32_t lo = 0, hi = items;   // invariant: s_off[lo] <= p < s_off[hi] (s_off[items] >= total)
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_off[mid] <= p) lo = mid; else hi = mid;
     }
-    if (ty1 < ty0 || tx1 < tx0 || ty1 >= 0xFFFFu || tx1 >= uint32_t(tiles_x)) continue;
-    for (uint32_t ty = ty0; ty <= ty1; ++ty)
-      for (uint32_t tx = tx0; tx <= tx1; ++tx, ++o) {
-        pk[o] = ty * uint32_t(tiles_x) + tx;
-        pv[o] = slot;
-      }
+    const uint2 r = s_rect[lo];
+    const uint32_t tx0 = r.x & 0xFFFFu, tx1 = r.x >> 16, ty0 = r.y & 0xFFFFu;
+    const uint32_t w = tx1 - tx0 + 1u;
+    const uint32_t k = p - s_off[lo];
+    const uint32_t dy = k / w;
+    pk[base + p] = (ty0 + dy) * uint32_t(tiles_x) + tx0 + (k - dy * w);
+    pv[base + p] = s_slot[lo];
   }
 }
 
@@ -91,18 +107,12 @@ k_ranges(const uint32_t* __restrict__ tk, uint32_t cap_pairs, const uint32_t* __
 
 }  // namespace
 
-cudaError_t launch_pair_scan(const uint32_t* slots, const uint2* rect, uint32_t cap, uint32_t* offsets,
-                             uint32_t* frame, uint32_t tc_slot, uint64_t* status, uint32_t epoch, cudaStream_t st) {
-  const uint32_t blocks = (cap + kScanTile - 1) / kScanTile;
-  if (blocks == 0) return cudaSuccess;
-  k_pair_scan<<<blocks, kScanThreads, 0, st>>>(slots, rect, cap, offsets, frame, tc_slot, status, epoch);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_duplicate(const uint32_t* slots, const uint2* rect, const uint32_t* offsets, uint32_t cap,
-                             uint32_t cap_pairs, int tiles_x, uint32_t* pk, uint32_t* pv, uint32_t* frame,
-                             int sm_count, cudaStream_t st) {
-  k_duplicate<<<sm_count * 8, 256, 0, st>>>(slots, rect, offsets, cap, cap_pairs, tiles_x, pk, pv, frame);
+cudaError_t launch_expand(const uint32_t* slots, const uint2* rect, uint32_t cap, uint32_t cap_pairs, int tiles_x,
+                          uint32_t* pk, uint32_t* pv, uint32_t* frame, uint32_t tc_slot, uint64_t* status,
+                          uint32_t epoch, cudaStream_t st) {
+  const uint32_t blocks = (cap + kExpTile - 1) / kExpTile;
+  if (blocks) k_expand<<<blocks, kExpThreads, 0, st>>>(slots, rect, cap, cap_pairs, tiles_x, pk, pv, frame, tc_slot,
+                                                       status, epoch);
   k_pairs_eff<<<1, 1, 0, st>>>(frame, cap_pairs);
   return cudaGetLastError();
 }

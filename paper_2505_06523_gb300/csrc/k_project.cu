@@ -5,7 +5,8 @@
 //   relative to it with small float32 offsets (the screen mean stays accurate to ~1e-7 of the
 //   node's extent instead of 1 ulp of the whole view distance).
 // k_project: one warp per render-list node (<= 64 Gaussians, 2 per lane), attribute-major loads
-//   (each plane is 64 contiguous floats per node, so every warp load is one 128-byte line).
+//   (each cluster's attributes are one contiguous block of planes of 64 floats, so every warp load
+//   is one 128-byte line and a cluster's data is one region of memory).
 //   Writes a 48-byte blend record, the tile rectangle and the float32 depth key per Gaussian;
 //   culled slots get the key 0xFFFFFFFF so that the depth sort moves them behind all visible ones.
 #include "dev_common.cuh"
@@ -79,8 +80,8 @@ k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* _
     const float4 bc = A.bound[node];
     const float4 r0 = ref[2 * ci], r1 = ref[2 * ci + 1];
     const bool comp = r1.w != 0.f;
-    const float* __restrict__ at = A.attr + size_t(node) * kSlots;
-    const size_t st = A.stride;
+    const float* __restrict__ at = A.attr + size_t(node) * A.stride;
+    constexpr size_t st = kSlots;   // floats between planes
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       const uint32_t j = lane + 32 * h;

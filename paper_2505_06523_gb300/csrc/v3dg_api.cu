@@ -181,7 +181,6 @@ v3dg_status ensure_work(v3dg_ctx* c) {
   ST(ensure(c, c->d_vals1, 4 * S));
   ST(ensure(c, c->d_rec, sizeof(float4) * 3 * S));
   ST(ensure(c, c->d_rect, sizeof(uint2) * S));
-  ST(ensure(c, c->d_off, 4 * S));
   ST(ensure(c, c->d_pk0, 4 * PP));
   ST(ensure(c, c->d_pk1, 4 * PP));
   ST(ensure(c, c->d_pv0, 4 * PP));
@@ -340,11 +339,9 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
   const uint32_t* dslots = in1 ? P<uint32_t>(c->d_vals1) : P<uint32_t>(c->d_vals0);
 
   stage_event(c, kStageBin);
-  CU(launch_pair_scan(dslots, P<uint2>(c->d_rect), c->cap_slots, P<uint32_t>(c->d_off), frame, 1,
-                      P<uint64_t>(c->d_status), next_epoch(c), c->stream));
-  CU(launch_duplicate(dslots, P<uint2>(c->d_rect), P<uint32_t>(c->d_off), c->cap_slots, c->cap_pairs, k.tiles_x,
-                      P<uint32_t>(c->d_pk0), P<uint32_t>(c->d_pv0), frame, sm, c->stream));
-  c->launches += 3;
+  CU(launch_expand(dslots, P<uint2>(c->d_rect), c->cap_slots, c->cap_pairs, k.tiles_x, P<uint32_t>(c->d_pk0),
+                   P<uint32_t>(c->d_pv0), frame, 1, P<uint64_t>(c->d_status), next_epoch(c), c->stream));
+  c->launches += 2;
 
   stage_event(c, kStageTileSort);
   const int n_tiles = k.tiles_x * k.tiles_y;
@@ -576,12 +573,12 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
   CU(cudaSetDevice(c->device));
   const uint32_t nn = d->n_nodes;
   const uint32_t coeffs = (d->sh_degree + 1) * (d->sh_degree + 1);
-  const size_t stride = size_t(nn) * kSlots;
   const int planes = attr_planes(int(coeffs));
+  const size_t block = size_t(planes) * kSlots;   // floats per cluster block
   std::vector<float4> own(nn), par(nn), bound(nn);
   std::vector<float> sigma(nn);
   std::vector<uint8_t> flags(nn), cnt(nn);
-  std::vector<float> attr(size_t(planes) * stride, 0.f);
+  std::vector<float> attr(size_t(nn) * block, 0.f);
   for (uint32_t n = 0; n < nn; ++n) {
     const float* s = d->own_sphere + 4 * size_t(n);
     own[n] = make_float4(s[0], s[1], s[2], s[3]);
@@ -606,15 +603,15 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
       rho = std::max(rho, std::sqrt(dx * dx + dy * dy + dz * dz));
       const float* ls = d->log_scales + 3 * g;
       smax = std::max(smax, std::exp(double(std::max(ls[0], std::max(ls[1], ls[2])))));
-      const size_t slot = size_t(n) * kSlots + j;
-      attr[kX * stride + slot] = m[0];
-      attr[kY * stride + slot] = m[1];
-      attr[kZ * stride + slot] = m[2];
-      attr[kOpacity * stride + slot] = d->opacity[g];
-      for (int q = 0; q < 3; ++q) attr[(kLs0 + q) * stride + slot] = ls[q];
-      for (int q = 0; q < 4; ++q) attr[(kQw + q) * stride + slot] = d->quats[4 * g + q];
+      float* blk = attr.data() + size_t(n) * block + j;   // plane p of this Gaussian: blk[p * 64]
+      blk[kX * kSlots] = m[0];
+      blk[kY * kSlots] = m[1];
+      blk[kZ * kSlots] = m[2];
+      blk[kOpacity * kSlots] = d->opacity[g];
+      for (int q = 0; q < 3; ++q) blk[(kLs0 + q) * kSlots] = ls[q];
+      for (int q = 0; q < 4; ++q) blk[(kQw + q) * kSlots] = d->quats[4 * g + q];
       const float* sh = d->sh + g * coeffs * 3;
-      for (uint32_t q = 0; q < coeffs * 3; ++q) attr[(kSh0 + q) * stride + slot] = sh[q];
+      for (uint32_t q = 0; q < coeffs * 3; ++q) blk[(kSh0 + q) * kSlots] = sh[q];
     }
     bound[n] = make_float4(cx, cy, cz, round_up_f(rho * (1.0 + 1e-6)));
     sigma[n] = round_up_f(smax * (1.0 + 1e-6));
@@ -659,7 +656,7 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
     t.count = P<uint8_t>(h.cnt);
     t.attr = P<float>(h.attr);
     t.n_nodes = h.n_nodes;
-    t.stride = h.n_nodes * uint32_t(kSlots);
+    t.stride = uint32_t(attr_planes(int(h.sh_coeffs)) * kSlots);
     t.sh_coeffs = h.sh_coeffs;
     t.pad = 0;
   }

@@ -10,7 +10,8 @@ constexpr int kTile = 16;              // 16x16 pixel tiles
 constexpr int kSlots = 64;             // Gaussian slots per cluster block on the device
 constexpr int kMaxShCoeffs = 16;       // degree 3
 
-// Attribute planes of one asset, each n_nodes * 64 floats (slot = node * 64 + j).
+// Attributes of one asset, one contiguous block per cluster: attr[node][plane][j], 64 floats per
+// plane (j = 0..63 is the Gaussian within the cluster).
 enum AttrPlane : int {
   kX = 0, kY, kZ, kOpacity, kLs0, kLs1, kLs2, kQw, kQx, kQy, kQz, kSh0,  // SH: kSh0 + 3 * coeff + channel
 };
@@ -26,9 +27,9 @@ struct AssetDev {
   const float* sigma_max;  // max over the node's Gaussians of exp(max log-scale)
   const uint8_t* flags;    // kLeaf | kRoot
   const uint8_t* count;    // Gaussians in the node, 1..64
-  const float* attr;       // attr_planes(sh_coeffs) planes of `stride` floats
+  const float* attr;       // n_nodes blocks of attr_planes(sh_coeffs) x 64 floats
   uint32_t n_nodes;
-  uint32_t stride;         // n_nodes * 64
+  uint32_t stride;         // floats per cluster block: attr_planes(sh_coeffs) * 64
   uint32_t sh_coeffs;      // (degree + 1)^2
   uint32_t pad;
 };
@@ -112,13 +113,11 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
                         const SortScratch& sc, uint32_t* err_flag, uint32_t& epoch, int sm_count,
                         cudaStream_t st, bool* result_in_1, int* launches);
 
-// Pair offsets (exclusive scan of tile counts in depth order) and duplication.
-cudaError_t launch_pair_scan(const uint32_t* sorted_slots, const uint2* rect, uint32_t cap_slots,
-                             uint32_t* offsets, uint32_t* frame, uint32_t tile_counter_slot,
-                             uint64_t* status, uint32_t epoch, cudaStream_t st);
-cudaError_t launch_duplicate(const uint32_t* sorted_slots, const uint2* rect, const uint32_t* offsets,
-                             uint32_t cap_slots, uint32_t cap_pairs, int tiles_x, uint32_t* pair_keys,
-                             uint32_t* pair_vals, uint32_t* frame, int sm_count, cudaStream_t st);
+// Expansion of the depth-sorted visible Gaussians into (tile, slot) pairs in depth order; writes
+// frame[kPairs] (the total) and frame[kPairsEff] (0 if the frame overflowed).
+cudaError_t launch_expand(const uint32_t* sorted_slots, const uint2* rect, uint32_t cap_slots, uint32_t cap_pairs,
+                          int tiles_x, uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* frame,
+                          uint32_t tile_counter_slot, uint64_t* status, uint32_t epoch, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const uint32_t* frame,
                           uint2* ranges, int n_tiles, int sm_count, cudaStream_t st);
 // work != nullptr: also count (evaluations, contributions) into work[0], work[1].
