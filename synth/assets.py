@@ -366,7 +366,7 @@ def cached_assets(seeds, n_leaves: int, workers: int | None = None, cache_dir: s
     if len(missing) > 1:
         import concurrent.futures as cf
         import multiprocessing as mp
-        workers = workers or min(len(missing), os.cpu_count() or 1)
+        workers = workers or min(len(missing), os.cpu_count() or 1, 4)   # each worker peaks at a few GB
         with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
             list(ex.map(_cached_asset_job, [(s, n_leaves, cache_dir) for s in missing]))
     return [cached_asset(s, n_leaves, cache_dir) for s in seeds]
