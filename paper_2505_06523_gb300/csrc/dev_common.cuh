@@ -24,18 +24,20 @@ __device__ __forceinline__ uint64_t pack_status(uint32_t epoch, uint64_t flag, u
   return (uint64_t(epoch) << 34) | (flag << 32) | uint64_t(value);
 }
 
-// Exclusive prefix of `agg` over all tiles before `tile` (decoupled look-back).  Tile t owns the
-// status word status[t * stride]; a word whose epoch differs from `epoch` counts as not yet
-// written, so the array never needs clearing between launches.  Called by one thread per chain.
-// Every wait is bounded: after kSpinLimit polls the thread sets *err, publishes what it has (so
-// that later tiles do not wait in turn) and returns.
-__device__ __forceinline__ uint32_t chained_exclusive(uint64_t* status, uint32_t stride, uint32_t tile,
-                                                      uint32_t agg, uint32_t epoch, uint32_t* err) {
-  if (tile == 0) {
-    st_status(status, pack_status(epoch, kFlagPrefix, agg));
-    return 0;
-  }
-  st_status(status + size_t(tile) * stride, pack_status(epoch, kFlagAgg, agg));
+// Decoupled look-back.  Tile t owns the status word status[t * stride]; a word whose epoch differs
+// from `epoch` counts as not yet written, so the array never needs clearing between launches.
+// chain_publish makes the tile's aggregate visible (tile 0 publishes its inclusive prefix);
+// chain_lookback then sums the earlier tiles' words back to the first inclusive prefix and
+// publishes the tile's own.  Every wait is bounded: after kSpinLimit polls the thread sets *err,
+// publishes what it has (so that later tiles do not wait in turn) and returns.
+__device__ __forceinline__ void chain_publish(uint64_t* status, uint32_t stride, uint32_t tile, uint32_t agg,
+                                              uint32_t epoch) {
+  st_status(status + size_t(tile) * stride, pack_status(epoch, tile == 0 ? kFlagPrefix : kFlagAgg, agg));
+}
+
+__device__ __forceinline__ uint32_t chain_lookback(uint64_t* status, uint32_t stride, uint32_t tile, uint32_t agg,
+                                                   uint32_t epoch, uint32_t* err) {
+  if (tile == 0) return 0;
   uint32_t excl = 0;
   int64_t j = int64_t(tile) - 1;
   uint32_t spins = 0;
@@ -56,6 +58,13 @@ __device__ __forceinline__ uint32_t chained_exclusive(uint64_t* status, uint32_t
   }
   st_status(status + size_t(tile) * stride, pack_status(epoch, kFlagPrefix, excl + agg));
   return excl;
+}
+
+// Exclusive prefix of `agg` over all tiles before `tile`: publish, then look back.
+__device__ __forceinline__ uint32_t chained_exclusive(uint64_t* status, uint32_t stride, uint32_t tile,
+                                                      uint32_t agg, uint32_t epoch, uint32_t* err) {
+  chain_publish(status, stride, tile, agg, epoch);
+  return chain_lookback(status, stride, tile, agg, epoch, err);
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

@@ -61,6 +61,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   __shared__ uint16_t s_wh[kWarps][kBins];   // per-warp digit counts, then per-warp exclusive offsets
   __shared__ uint32_t s_start[kBins];        // block-local start of each digit
   __shared__ int32_t s_goff[kBins];          // global destination offset minus local start
+  __shared__ uint32_t s_cnt[kBins];          // the tile's digit counts
   __shared__ uint32_t s_scan[kWarps + 1];
   __shared__ uint32_t s_tile;
 
@@ -72,6 +73,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   const uint32_t tile = s_tile;
   if (tile >= ntiles) return;  // the grid is sized by capacity: surplus blocks leave at once
   for (int i = tid; i < kWarps * kBins / 2; i += kSortThreads) reinterpret_cast<uint32_t*>(&s_wh[0][0])[i] = 0;
+  if (tid < kBins) s_cnt[tid] = 0;
   __syncthreads();
   const uint32_t base = tile * kSortTile + warp * (kSortItems * 32);
 
@@ -83,6 +85,13 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     key[i] = ok ? kin[idx] : 0xFFFFFFFFu;
     val[i] = kImplicit ? idx : (ok ? vin[idx] : 0u);
   }
+  // the tile's digit counts first, published at once, so that later tiles' look-backs find them
+  // while this tile is still ranking
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i)
+    if (base + i * 32 + lane < n) atomicAdd(&s_cnt[(key[i] >> shift) & dmask], 1u);
+  __syncthreads();
+  if (tid < kBins) chain_publish(status + tid, kBins, tile, s_cnt[tid], epoch);
   // warp-level stable ranking: item-major, then lane order
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
@@ -116,7 +125,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   const uint32_t start = block_exclusive_scan<kWarps>(cnt, s_scan, &total);
   if (tid < kBins) {
     s_start[tid] = start;
-    const uint32_t excl = chained_exclusive(status + tid, kBins, tile, cnt, epoch, err);
+    const uint32_t excl = chain_lookback(status + tid, kBins, tile, cnt, epoch, err);
     s_goff[tid] = int32_t(gexcl[tid] + excl) - int32_t(start);
   }
   __syncthreads();
