@@ -109,7 +109,10 @@ enum {
   V3DG_OPT_STAGE_TIMING = 2, /* 1: record CUDA events around every stage (see v3dg_stage_times) */
   V3DG_OPT_CAP_NODES = 3,    /* current render-list capacity in clusters (>= 64); grows on demand */
   V3DG_OPT_CAP_PAIRS = 4,    /* current (tile, Gaussian) pair capacity (>= 4096); grows on demand */
-  V3DG_OPT_COUNT_WORK = 5    /* 1: the blend also counts its evaluations (v3dg_stats.blend_*) */
+  V3DG_OPT_COUNT_WORK = 5,   /* 1: the blend also counts its evaluations (v3dg_stats.blend_*) */
+  V3DG_OPT_SPLIT_PAIRS = 6   /* tiles with at least this many pairs are blended as four 8x8
+                                quadrants by separate blocks (default 16384; the image does not
+                                depend on it) */
 };
 
 /* Create a context on CUDA device `device`.  `alloc` may be NULL (cudaMalloc/cudaFree). */

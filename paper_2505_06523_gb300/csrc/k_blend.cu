@@ -1,7 +1,7 @@
 // Per-tile front-to-back alpha blending (Sec. 2.1): C = sum_i c_i a_i prod_{j<i} (1 - a_j).
 //
-// One 256-thread block per 16x16 tile (persistent blocks take tiles heaviest-first: tiles differ
-// in cost by orders of magnitude).  The tile's depth-ordered records are taken in batches of up to
+// One 256-thread block per 16x16 tile, or per 8x8 quadrant of a tile with a long list
+// (persistent blocks take work items heaviest-first: tiles differ in cost by orders of magnitude).  The tile's depth-ordered records are taken in batches of up to
 // 256; each batch runs in two phases:
 //  - record-parallel test: the batch's (record, pixel) pairs -- every pixel of the record's
 //    alpha >= 1/255 pixel box that is still accumulating -- are spread evenly over the threads;
@@ -49,8 +49,8 @@ __device__ __forceinline__ uint32_t rowpair_mask(int y0, int y1) {
 
 template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads, 4)
-k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, uint32_t* __restrict__ tile_counter,
-        int n_tiles, const uint32_t* __restrict__ pv, const float4* __restrict__ rec, uint32_t cap_slots, int width,
+k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, const uint32_t* __restrict__ n_items,
+        uint32_t* __restrict__ tile_counter, const uint32_t* __restrict__ pv, const float4* __restrict__ rec, uint32_t cap_slots, int width,
         int height, int tiles_x, float* __restrict__ rgb, float* __restrict__ t_out,
         unsigned long long* __restrict__ work, const uint32_t* __restrict__ frame, uint32_t* __restrict__ sticky) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -78,11 +78,16 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, ui
     __syncthreads();
     const uint32_t next = s_next;
     __syncthreads();
-    if (next >= uint32_t(n_tiles)) break;
-    const int tile = int(order[next]);
+    if (next >= *n_items) break;
+    const uint32_t item = items[next];
+    const int tile = int(item & 0xFFFFFFu), region = int(item >> 24);
     const int tx = tile % tiles_x, ty = tile / tiles_x;
+    // the item's pixel rectangle within the tile: the whole tile or one 8x8 quadrant
+    const int qx0 = region ? 8 * ((region - 1) & 1) : 0, qy0 = region ? 8 * ((region - 1) >> 1) : 0;
+    const int qx1 = region ? qx0 + 7 : 15, qy1 = region ? qy0 + 7 : 15;
     const int px = tx * 16 + lx, py = ty * 16 + ly;
-    const bool inside = px < width && py < height;
+    const bool mine = lx >= qx0 && lx <= qx1 && ly >= qy0 && ly <= qy1;
+    const bool inside = px < width && py < height && mine;
     const uint2 range = ranges[tile];
     float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
     bool done = !inside;
@@ -98,7 +103,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, ui
       if (act == 0 || sp >= range.y) break;
       // fill the batch with the next records whose box reaches a live row pair, in list order
       uint32_t q = 0;
-      if (act == (1u << kBlendWarps) - 1u) {   // every row pair live: every record is relevant
+      if (region == 0 && act == (1u << kBlendWarps) - 1u) {   // every row pair live: every record is relevant
         q = min(uint32_t(kBlendThreads), range.y - sp);
         if (threadIdx.x < q) s_qslot[threadIdx.x] = pv[sp + threadIdx.x];
         sp += q;
@@ -115,7 +120,8 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, ui
               if (sl[k] < cap_slots) {
                 int x0, x1, y0, y1;
                 box_in_tile(rec[3 * size_t(sl[k]) + 2], tx, ty, &x0, &x1, &y0, &y1);
-                if (x0 <= x1 && (rowpair_mask(y0, y1) & act)) hits |= 1u << k;
+                if (x0 <= qx1 && x1 >= qx0 && y0 <= qy1 && y1 >= qy0 && (rowpair_mask(y0, y1) & act))
+                  hits |= 1u << k;
               }
             }
           }
@@ -155,6 +161,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, ui
           s_b[threadIdx.x] = r2.x;
           int x0, x1, y0, y1;
           box_in_tile(r2, tx, ty, &x0, &x1, &y0, &y1);
+          x0 = max(x0, qx0); x1 = min(x1, qx1); y0 = max(y0, qy0); y1 = min(y1, qy1);
           if (x0 <= x1 && y0 <= y1) {
             area = uint32_t((x1 - x0 + 1) * (y1 - y0 + 1));
             s_box[threadIdx.x] = uint32_t(x0) | (uint32_t(x1) << 8) | (uint32_t(y0) << 16) | (uint32_t(y1) << 24);
@@ -223,7 +230,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, ui
       }
       __syncthreads();
     }
-    if (inside) {
+    if (inside) {   // this item's pixels only
       const size_t p = size_t(py) * width + px;
       rgb[3 * p + 0] = cr;
       rgb[3 * p + 1] = cg;
@@ -245,15 +252,20 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, ui
   }
 }
 
-// Tile order, heaviest first: one block buckets the tiles by floor(log2(pairs + 1)) (descending).
-__global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, int n_tiles,
-                                                     uint32_t* __restrict__ order) {
+// Work items, heaviest first.  A tile with at least split_pairs pairs becomes four items, one
+// per 8x8 quadrant (each scans the tile's list by boxes but stages and evaluates only the
+// records that reach its quadrant, so a long list is spread over four blocks); other tiles are
+// one item.  Item = tile | region << 24 (region 0: whole tile, 1 + q: quadrant q).  One block
+// buckets the items by floor(log2(pairs + 1)), descending.
+__global__ void __launch_bounds__(1024) k_blend_items(const uint2* __restrict__ ranges, int n_tiles,
+                                                      uint32_t split_pairs, uint32_t* __restrict__ items,
+                                                      uint32_t* __restrict__ n_items) {
   __shared__ uint32_t s_hist[32];
   if (threadIdx.x < 32) s_hist[threadIdx.x] = 0;
   __syncthreads();
   for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-    const uint2 r = ranges[t];
-    atomicAdd(&s_hist[__clz(r.y - r.x + 1u)], 1u);   // clz: 0 for the heaviest bucket
+    const uint32_t len = ranges[t].y - ranges[t].x;
+    atomicAdd(&s_hist[__clz(len + 1u)], len >= split_pairs ? 4u : 1u);   // clz: 0 for the heaviest
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -265,30 +277,38 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
       if (threadIdx.x >= d) incl += t;
     }
     s_hist[threadIdx.x] = incl - v;   // cursor: first position of the bucket
+    if (threadIdx.x == 31) *n_items = incl;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-    const uint2 r = ranges[t];
-    order[atomicAdd(&s_hist[__clz(r.y - r.x + 1u)], 1u)] = uint32_t(t);
+    const uint32_t len = ranges[t].y - ranges[t].x;
+    if (len >= split_pairs) {
+      const uint32_t pos = atomicAdd(&s_hist[__clz(len + 1u)], 4u);
+      for (uint32_t q = 0; q < 4; ++q) items[pos + q] = uint32_t(t) | ((q + 1u) << 24);
+    } else {
+      items[atomicAdd(&s_hist[__clz(len + 1u)], 1u)] = uint32_t(t);
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_blend(const uint2* ranges, uint32_t* order, uint32_t* tile_counter, const uint32_t* pv,
+cudaError_t launch_blend(const uint2* ranges, uint32_t* items, uint32_t* tile_counter, const uint32_t* pv,
                          const float4* rec, uint32_t cap_slots, const CamConst& cam, float* rgb, float* t_out,
-                         unsigned long long* work, const uint32_t* frame, uint32_t* sticky, int sm_count,
-                         cudaStream_t st) {
+                         unsigned long long* work, const uint32_t* frame, uint32_t* sticky, uint32_t split_pairs,
+                         int sm_count, cudaStream_t st) {
   const int n_tiles = cam.tiles_x * cam.tiles_y;
   if (n_tiles == 0) return cudaSuccess;
-  k_tile_order<<<1, 1024, 0, st>>>(ranges, n_tiles, order);
-  const int grid = std::min(n_tiles, sm_count * 4);   // 4 resident blocks per SM (56 registers)
+  uint32_t* n_items = items + 4 * size_t(n_tiles);
+  k_blend_items<<<1, 1024, 0, st>>>(ranges, n_tiles, split_pairs, items, n_items);
+  const int grid = std::min(4 * n_tiles, sm_count * 4);   // 4 resident blocks per SM (56 registers)
   if (work)
-    k_blend<true><<<grid, kBlendThreads, 0, st>>>(ranges, order, tile_counter, n_tiles, pv, rec, cap_slots, cam.width,
-                                                  cam.height, cam.tiles_x, rgb, t_out, work, frame, sticky);
+    k_blend<true><<<grid, kBlendThreads, 0, st>>>(ranges, items, n_items, tile_counter, pv, rec, cap_slots,
+                                                  cam.width, cam.height, cam.tiles_x, rgb, t_out, work, frame, sticky);
   else
-    k_blend<false><<<grid, kBlendThreads, 0, st>>>(ranges, order, tile_counter, n_tiles, pv, rec, cap_slots, cam.width,
-                                                   cam.height, cam.tiles_x, rgb, t_out, nullptr, frame, sticky);
+    k_blend<false><<<grid, kBlendThreads, 0, st>>>(ranges, items, n_items, tile_counter, pv, rec, cap_slots,
+                                                   cam.width, cam.height, cam.tiles_x, rgb, t_out, nullptr, frame,
+                                                   sticky);
   return cudaGetLastError();
 }
 

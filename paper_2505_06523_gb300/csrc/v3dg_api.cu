@@ -77,6 +77,7 @@ struct v3dg_ctx {
   uint32_t epoch = 1;
   uint64_t launches = 0;
   bool sync_check = true, stage_timing = false, count_work = false;
+  uint32_t split_pairs = 16384;
   unsigned long long work[2] = {0, 0};
   cudaEvent_t ev[kStages + 1] = {};
 };
@@ -360,7 +361,7 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
 
   stage_event(c, kStageRanges);
   ST(ensure(c, c->d_ranges, sizeof(uint2) * size_t(n_tiles)));
-  ST(ensure(c, c->d_order, sizeof(uint32_t) * size_t(n_tiles)));
+  ST(ensure(c, c->d_order, sizeof(uint32_t) * (4 * size_t(n_tiles) + 1)));
   CU(launch_ranges(tk, c->cap_pairs, frame, P<uint2>(c->d_ranges), n_tiles, sm, c->stream));
   c->launches += 1;
 
@@ -370,7 +371,8 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
   if (work) CU(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), c->stream));
   // d_misc[12], [13]: sticky overflow / timeout flags of all frames since the last v3dg_frame_stats
   CU(launch_blend(P<uint2>(c->d_ranges), P<uint32_t>(c->d_order), frame + kTileCounters + 10, tv, P<float4>(c->d_rec),
-                  c->cap_slots, k, rgb, t_out, work, frame, P<uint32_t>(c->d_misc) + 12, sm, c->stream));
+                  c->cap_slots, k, rgb, t_out, work, frame, P<uint32_t>(c->d_misc) + 12, c->split_pairs, sm,
+                  c->stream));
   c->launches += 2;
   if (work)
     CU(cudaMemcpyAsync(c->h_tmp + kFrameWords, work, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
@@ -553,6 +555,10 @@ v3dg_status v3dg_set_option(v3dg_ctx* c, int option, int64_t value) {
     case V3DG_OPT_SYNC_CHECK: c->sync_check = value != 0; break;
     case V3DG_OPT_STAGE_TIMING: c->stage_timing = value != 0; break;
     case V3DG_OPT_COUNT_WORK: c->count_work = value != 0; break;
+    case V3DG_OPT_SPLIT_PAIRS:
+      if (value < 1 || value > 0xFFFFFFFFll) return fail(c, V3DG_EINVAL, "split threshold out of range");
+      c->split_pairs = uint32_t(value);
+      break;
     case V3DG_OPT_CAP_NODES:
       if (value < 64 || value > int64_t(kMaxNodes)) return fail(c, V3DG_EINVAL, "node capacity out of range");
       c->cap_nodes = uint32_t(value);

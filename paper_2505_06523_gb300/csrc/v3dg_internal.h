@@ -123,10 +123,11 @@ cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const u
 // work != nullptr: also count (evaluations, contributions) into work[0], work[1].
 // sticky[0] |= frame[kOverflow], sticky[1] |= frame[kTimeout] (the flags of every frame since the
 // host last cleared them).
-// order: n_tiles words of scratch (the heaviest-first tile order); tile_counter: a zeroed word.
-cudaError_t launch_blend(const uint2* ranges, uint32_t* order, uint32_t* tile_counter, const uint32_t* pair_vals,
+// items: 4 * n_tiles + 1 words of scratch (the heaviest-first work items and their count);
+// tile_counter: a zeroed word.
+cudaError_t launch_blend(const uint2* ranges, uint32_t* items, uint32_t* tile_counter, const uint32_t* pair_vals,
                          const float4* rec, uint32_t cap_slots, const CamConst& cam, float* rgb, float* t_out,
-                         unsigned long long* work, const uint32_t* frame, uint32_t* sticky, int sm_count,
-                         cudaStream_t st);
+                         unsigned long long* work, const uint32_t* frame, uint32_t* sticky, uint32_t split_pairs,
+                         int sm_count, cudaStream_t st);
 
 }  // namespace v3dg

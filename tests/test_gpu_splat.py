@@ -183,3 +183,14 @@ def test_render_twice_after_one_select(Context, small_asset):
         c = ctx.render()[0]
     assert float(a.abs().sum()) > 0
     assert (a == b).all() and (a == c).all()
+
+
+def test_quadrant_split_is_bit_identical(Context, tiny_asset, small_asset):
+    """Blending long tiles as four quadrants (here: every tile) changes no pixel."""
+    from paper_2505_06523_gb300._native import V3DG_OPT_SPLIT_PAIRS
+    inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+    cam = scenes.crowd_camera(40, 640, 360)
+    whole = _frame(Context, [tiny_asset, small_asset], inst, cam, 1.0, {V3DG_OPT_SPLIT_PAIRS: 1 << 30})
+    split = _frame(Context, [tiny_asset, small_asset], inst, cam, 1.0, {V3DG_OPT_SPLIT_PAIRS: 1})
+    assert float(np.abs(whole["rgb"]).sum()) > 0
+    assert (whole["rgb"] == split["rgb"]).all() and (whole["T"] == split["T"]).all()
