@@ -54,6 +54,22 @@ def dist_env():
     return rank, world, local
 
 
+def replica_frames(rank: int, world: int, count: int, frames: int = 300) -> list[int]:
+    """Walk frames rendered by one replica: each rank starts at its own offset (no collective)."""
+    return [(rank * 37 + 7 * s) % frames for s in range(count)]
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Largest value over all ranks (the slowest replica sets the time); identity for one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_scene(n_assets=N_ASSETS, n_inst=N_INST):
     from synth import scenes
     from synth.assets import cached_assets
@@ -202,7 +218,7 @@ def main():
         ctx.load_hierarchy(a)
     ctx.set_instances(inst)
     cams = [scenes.crowd_camera(t) for t in range(300)]
-    frame_ids = [(rank * 37 + 7 * s) % 300 for s in range(args.warmup + args.steps)]
+    frame_ids = replica_frames(rank, world, args.warmup + args.steps)
     rgb = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32, device=f"cuda:{local}")
     stream = ctx.stream
 
@@ -235,10 +251,7 @@ def main():
     stats = ctx.frame_stats()   # overflow / timeout flags are sticky over every timed frame
     if stats["overflow"] or stats["timeout"]:
         raise RuntimeError(f"a frame of the timed region was invalid: {stats}")
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     value = world * args.steps / (total_ms / 1000.0)
 
     # per-stage device times over the same frames: replay them with stage events (synchronous, so
@@ -281,11 +294,7 @@ def main():
         ctx.select(cams[frame_ids[s % len(frame_ids)]], args.tau)
         ctx.render_host(host_rgb)
     e2e_s = time.perf_counter() - t0
-    e2e_val = world * e2e_steps / e2e_s if world == 1 else None
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = world * e2e_steps / float(t.item())
+    e2e_val = world * e2e_steps / max_over_ranks(e2e_s, world)
     h2d = inst.n * 256
     d2h = WIDTH * HEIGHT * 3 * 4
 
@@ -297,7 +306,7 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            v, spent, desc = cpu_baseline(assets, inst, args.tau)
+            v, spent, desc = cpu_baseline(assets, inst, args.tau, inst_frac=0.02, n_pix=16)
             cpu = {"value": v, "unit": "frames/s", "cores": 1, "kind": "oracle",
                    "sample": desc + f" ({spent:.0f} s of CPU work, single-threaded numpy)"}
         line = {

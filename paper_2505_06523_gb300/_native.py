@@ -21,6 +21,7 @@ V3DG_OPT_CAP_NODES = 3
 V3DG_OPT_CAP_PAIRS = 4
 V3DG_OPT_COUNT_WORK = 5
 V3DG_OPT_SPLIT_PAIRS = 6
+V3DG_OPT_ATTR_FP16 = 7
 
 
 class V3dgError(RuntimeError):

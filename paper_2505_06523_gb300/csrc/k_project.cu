@@ -9,12 +9,20 @@
 //   is one 128-byte line and a cluster's data is one region of memory).
 //   Writes a 48-byte blend record, the tile rectangle and the float32 depth key per Gaussian;
 //   culled slots get the key 0xFFFFFFFF so that the depth sort moves them behind all visible ones.
+#include <cuda_fp16.h>
+
 #include "dev_common.cuh"
 
 namespace v3dg {
 namespace {
 
 constexpr int kProjThreads = 256;
+
+// One colour value (opacity or SH) of Gaussian j from a cluster block's colour section.
+__device__ __forceinline__ float ld_color(const unsigned char* col, bool half, int plane, int j) {
+  return half ? __half2float(reinterpret_cast<const __half*>(col)[plane * kSlots + j])
+              : reinterpret_cast<const float*>(col)[plane * kSlots + j];
+}
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kMinOpacity = 0.0039215689f;  // smallest float >= 1/255 (0x3b808081)
 
@@ -80,8 +88,11 @@ k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* _
     const float4 bc = A.bound[node];
     const float4 r0 = ref[2 * ci], r1 = ref[2 * ci + 1];
     const bool comp = r1.w != 0.f;
-    const float* __restrict__ at = A.attr + size_t(node) * A.stride;
-    constexpr size_t st = kSlots;   // floats between planes
+    const unsigned char* blk = A.attr + size_t(node) * A.stride;
+    const float* __restrict__ at = reinterpret_cast<const float*>(blk);   // geometry planes
+    const unsigned char* col = blk + size_t(kGeoPlanes) * kSlots * 4;     // colour planes
+    const bool half = A.half_color != 0;
+    constexpr size_t st = kSlots;   // values between planes
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       const uint32_t j = lane + 32 * h;
@@ -91,7 +102,7 @@ k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* _
         continue;
       }
       const float mx = at[kX * st + j], my = at[kY * st + j], mz = at[kZ * st + j];
-      const float op = at[kOpacity * st + j];
+      const float op = ld_color(col, half, kOpacity, int(j));
       // float32 depth key: ((M20 x + M21 y) + M22 z) + M23, every step rounded (no fusion)
       const float z32 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(I.m[8], mx), __fmul_rn(I.m[9], my)),
                                             __fmul_rn(I.m[10], mz)), I.m[11]);
@@ -199,20 +210,20 @@ k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* _
           Y[15] = -kY3a * dx * (xx - 3.f * yy);
         }
       }
-      float col[3];
+      float rgb[3];
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.f;
 #pragma unroll
         for (int k = 0; k < kMaxShCoeffs; ++k)
-          if (k < nsh) acc = fmaf(Y[k], at[(kSh0 + 3 * k + ch) * st + j], acc);
-        col[ch] = fmaxf(acc + 0.5f, 0.f);
+          if (k < nsh) acc = fmaf(Y[k], ld_color(col, half, kSh0 + 3 * k + ch, int(j)), acc);
+        rgb[ch] = fmaxf(acc + 0.5f, 0.f);
       }
       const uint32_t origin = uint32_t(tx0) | (uint32_t(ty0) << 16);
       float4* rp = rec + 3 * slot;
       rp[0] = make_float4(u_rel, v_rel, -0.5f * kLog2e * ia, -kLog2e * ib);
-      rp[1] = make_float4(-0.5f * kLog2e * ic, log2f(op), col[0], col[1]);
-      rp[2] = make_float4(col[2], __uint_as_float(origin), __uint_as_float(uint32_t(x0) | (uint32_t(x1) << 16)),
+      rp[1] = make_float4(-0.5f * kLog2e * ic, log2f(op), rgb[0], rgb[1]);
+      rp[2] = make_float4(rgb[2], __uint_as_float(origin), __uint_as_float(uint32_t(x0) | (uint32_t(x1) << 16)),
                           __uint_as_float(uint32_t(y0) | (uint32_t(y1) << 16)));
       rect[slot] = make_uint2(uint32_t(tx0) | (uint32_t(tx1) << 16), uint32_t(ty0) | (uint32_t(ty1) << 16));
       keys[slot] = __float_as_uint(z32);

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "v3dg.h"
@@ -28,6 +29,7 @@ struct DevBuf {
 
 struct AssetHost {
   uint32_t n_gauss = 0, n_nodes = 0, sh_coeffs = 0, gpg = 0;
+  bool half_color = false;
   std::vector<uint32_t> node_first;
   DevBuf own, par, bound, sigma, flags, cnt, attr;
 };
@@ -78,6 +80,7 @@ struct v3dg_ctx {
   uint64_t launches = 0;
   bool sync_check = true, stage_timing = false, count_work = false;
   uint32_t split_pairs = 16384;
+  bool attr_fp16 = false;   // store opacity and SH of the next loaded assets as float16
   unsigned long long work[2] = {0, 0};
   cudaEvent_t ev[kStages + 1] = {};
 };
@@ -555,6 +558,7 @@ v3dg_status v3dg_set_option(v3dg_ctx* c, int option, int64_t value) {
     case V3DG_OPT_SYNC_CHECK: c->sync_check = value != 0; break;
     case V3DG_OPT_STAGE_TIMING: c->stage_timing = value != 0; break;
     case V3DG_OPT_COUNT_WORK: c->count_work = value != 0; break;
+    case V3DG_OPT_ATTR_FP16: c->attr_fp16 = value != 0; break;
     case V3DG_OPT_SPLIT_PAIRS:
       if (value < 1 || value > 0xFFFFFFFFll) return fail(c, V3DG_EINVAL, "split threshold out of range");
       c->split_pairs = uint32_t(value);
@@ -579,12 +583,12 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
   CU(cudaSetDevice(c->device));
   const uint32_t nn = d->n_nodes;
   const uint32_t coeffs = (d->sh_degree + 1) * (d->sh_degree + 1);
-  const int planes = attr_planes(int(coeffs));
-  const size_t block = size_t(planes) * kSlots;   // floats per cluster block
+  const bool half = c->attr_fp16;
+  const size_t block = cluster_block_bytes(int(coeffs), half);   // bytes per cluster block
   std::vector<float4> own(nn), par(nn), bound(nn);
   std::vector<float> sigma(nn);
   std::vector<uint8_t> flags(nn), cnt(nn);
-  std::vector<float> attr(size_t(nn) * block, 0.f);
+  std::vector<unsigned char> attr(size_t(nn) * block, 0);
   for (uint32_t n = 0; n < nn; ++n) {
     const float* s = d->own_sphere + 4 * size_t(n);
     own[n] = make_float4(s[0], s[1], s[2], s[3]);
@@ -609,15 +613,23 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
       rho = std::max(rho, std::sqrt(dx * dx + dy * dy + dz * dz));
       const float* ls = d->log_scales + 3 * g;
       smax = std::max(smax, std::exp(double(std::max(ls[0], std::max(ls[1], ls[2])))));
-      float* blk = attr.data() + size_t(n) * block + j;   // plane p of this Gaussian: blk[p * 64]
-      blk[kX * kSlots] = m[0];
-      blk[kY * kSlots] = m[1];
-      blk[kZ * kSlots] = m[2];
-      blk[kOpacity * kSlots] = d->opacity[g];
-      for (int q = 0; q < 3; ++q) blk[(kLs0 + q) * kSlots] = ls[q];
-      for (int q = 0; q < 4; ++q) blk[(kQw + q) * kSlots] = d->quats[4 * g + q];
+      unsigned char* cb = attr.data() + size_t(n) * block;
+      float* geo = reinterpret_cast<float*>(cb) + j;   // geometry plane p of this Gaussian: geo[p * 64]
+      geo[kX * kSlots] = m[0];
+      geo[kY * kSlots] = m[1];
+      geo[kZ * kSlots] = m[2];
+      for (int q = 0; q < 3; ++q) geo[(kLs0 + q) * kSlots] = ls[q];
+      for (int q = 0; q < 4; ++q) geo[(kQw + q) * kSlots] = d->quats[4 * g + q];
+      unsigned char* col = cb + size_t(kGeoPlanes) * kSlots * 4;
+      auto put = [&](int plane, float v) {
+        if (half)
+          reinterpret_cast<__half*>(col)[plane * kSlots + j] = __float2half_rn(v);
+        else
+          reinterpret_cast<float*>(col)[plane * kSlots + j] = v;
+      };
+      put(kOpacity, d->opacity[g]);
       const float* sh = d->sh + g * coeffs * 3;
-      for (uint32_t q = 0; q < coeffs * 3; ++q) blk[(kSh0 + q) * kSlots] = sh[q];
+      for (uint32_t q = 0; q < coeffs * 3; ++q) put(int(kSh0 + q), sh[q]);
     }
     bound[n] = make_float4(cx, cy, cz, round_up_f(rho * (1.0 + 1e-6)));
     sigma[n] = round_up_f(smax * (1.0 + 1e-6));
@@ -633,6 +645,7 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
   a.n_nodes = nn;
   a.sh_coeffs = coeffs;
   a.gpg = d->gaussians_per_group;
+  a.half_color = half;
   a.node_first.assign(d->node_first, d->node_first + nn);
   auto up = [&](DevBuf& b, const void* src, size_t bytes) -> v3dg_status {
     ST(dalloc(c, b, bytes));
@@ -644,7 +657,7 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
       (s = up(a.bound, bound.data(), sizeof(float4) * nn)) != V3DG_OK ||
       (s = up(a.sigma, sigma.data(), sizeof(float) * nn)) != V3DG_OK ||
       (s = up(a.flags, flags.data(), nn)) != V3DG_OK || (s = up(a.cnt, cnt.data(), nn)) != V3DG_OK ||
-      (s = up(a.attr, attr.data(), sizeof(float) * attr.size())) != V3DG_OK) {
+      (s = up(a.attr, attr.data(), attr.size())) != V3DG_OK) {
     DevBuf* bs[] = {&a.own, &a.par, &a.bound, &a.sigma, &a.flags, &a.cnt, &a.attr};
     for (DevBuf* b : bs) dfree(c, *b);
     return s;
@@ -660,11 +673,11 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
     t.sigma_max = P<float>(h.sigma);
     t.flags = P<uint8_t>(h.flags);
     t.count = P<uint8_t>(h.cnt);
-    t.attr = P<float>(h.attr);
+    t.attr = P<unsigned char>(h.attr);
     t.n_nodes = h.n_nodes;
-    t.stride = uint32_t(attr_planes(int(h.sh_coeffs)) * kSlots);
+    t.stride = uint32_t(cluster_block_bytes(int(h.sh_coeffs), h.half_color));
     t.sh_coeffs = h.sh_coeffs;
-    t.pad = 0;
+    t.half_color = h.half_color ? 1u : 0u;
   }
   ST(ensure(c, c->d_assets, sizeof(AssetDev) * table.size()));
   CU(cudaMemcpy(c->d_assets.p, table.data(), sizeof(AssetDev) * table.size(), cudaMemcpyHostToDevice));

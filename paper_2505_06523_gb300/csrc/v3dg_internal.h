@@ -10,12 +10,16 @@ constexpr int kTile = 16;              // 16x16 pixel tiles
 constexpr int kSlots = 64;             // Gaussian slots per cluster block on the device
 constexpr int kMaxShCoeffs = 16;       // degree 3
 
-// Attributes of one asset, one contiguous block per cluster: attr[node][plane][j], 64 floats per
-// plane (j = 0..63 is the Gaussian within the cluster).
-enum AttrPlane : int {
-  kX = 0, kY, kZ, kOpacity, kLs0, kLs1, kLs2, kQw, kQx, kQy, kQz, kSh0,  // SH: kSh0 + 3 * coeff + channel
-};
-constexpr int attr_planes(int sh_coeffs) { return kSh0 + 3 * sh_coeffs; }
+// Attributes of one asset, one contiguous block per cluster: planes of 64 values (j = 0..63 is
+// the Gaussian within the cluster).  First the geometry planes, always float32, then the colour
+// planes (opacity, then SH coefficient-major, channel-minor), float32 or -- for assets loaded with
+// V3DG_OPT_ATTR_FP16 -- float16.
+enum GeoPlane : int { kX = 0, kY, kZ, kLs0, kLs1, kLs2, kQw, kQx, kQy, kQz, kGeoPlanes };
+enum ColorPlane : int { kOpacity = 0, kSh0 = 1 };   // SH: kSh0 + 3 * coeff + channel
+constexpr int color_planes(int sh_coeffs) { return kSh0 + 3 * sh_coeffs; }
+constexpr size_t cluster_block_bytes(int sh_coeffs, bool half) {
+  return size_t(kGeoPlanes) * kSlots * 4 + size_t(color_planes(sh_coeffs)) * kSlots * (half ? 2 : 4);
+}
 
 // Node flags.
 constexpr uint8_t kLeaf = 1, kRoot = 2;
@@ -27,11 +31,11 @@ struct AssetDev {
   const float* sigma_max;  // max over the node's Gaussians of exp(max log-scale)
   const uint8_t* flags;    // kLeaf | kRoot
   const uint8_t* count;    // Gaussians in the node, 1..64
-  const float* attr;       // n_nodes blocks of attr_planes(sh_coeffs) x 64 floats
+  const unsigned char* attr;  // n_nodes cluster blocks of `stride` bytes
   uint32_t n_nodes;
-  uint32_t stride;         // floats per cluster block: attr_planes(sh_coeffs) * 64
+  uint32_t stride;         // bytes per cluster block: cluster_block_bytes(sh_coeffs, half_color)
   uint32_t sh_coeffs;      // (degree + 1)^2
-  uint32_t pad;
+  uint32_t half_color;     // 1: opacity and SH stored as float16
 };
 
 // Per (frame, instance) constants, computed on the host in FP64 (128-byte aligned, 256 B).

@@ -194,3 +194,33 @@ def test_quadrant_split_is_bit_identical(Context, tiny_asset, small_asset):
     split = _frame(Context, [tiny_asset, small_asset], inst, cam, 1.0, {V3DG_OPT_SPLIT_PAIRS: 1})
     assert float(np.abs(whole["rgb"]).sum()) > 0
     assert (whole["rgb"] == split["rgb"]).all() and (whole["T"] == split["T"]).all()
+
+
+def _fp16_rounded(asset):
+    import copy
+    a = copy.copy(asset)
+    a.sh = asset.sh.astype(np.float16).astype(np.float32)
+    a.opacity = asset.opacity.astype(np.float16).astype(np.float32)
+    return a
+
+
+@pytest.mark.parametrize("view", [0, 1])
+def test_fp16_attributes_parity(Context, tiny_asset, view):
+    """Opacity and SH stored as float16: parity with the oracle on the rounded attributes, and
+    PSNR >= 50 dB against the oracle on the float32 attributes."""
+    from paper_2505_06523_gb300._native import V3DG_OPT_ATTR_FP16
+    cam = [scenes.tiny_camera(), scenes.look_at((1.2, -1.6, 0.9), (0, 0, 0), 200, 136, 70.0)][view]
+    inst = scenes.single_instance()
+    out = _frame(Context, [tiny_asset], inst, cam, 1.0, {V3DG_OPT_ATTR_FP16: 1})
+    a16 = _fp16_rounded(tiny_asset)
+    cut = oracle.select([a16], inst, cam, 1.0)
+    assert_cut_parity(out["cut"], cut)
+    p16 = oracle.project([a16], inst, cam, cut)
+    assert_projection_parity(out["proj"], p16)
+    assert_pairs_parity(out["pairs"], p16, cam)
+    C16, T16, B16 = oracle.render_image(p16, cam.width, cam.height)
+    err, ps, _ = image_errors(out["rgb"], C16, B16)
+    assert err <= IMG_ABS and ps >= PSNR_MIN, (err, ps)
+    p32 = oracle.project([tiny_asset], inst, cam, cut)
+    C32, _, _ = oracle.render_image(p32, cam.width, cam.height)
+    assert oracle.psnr(out["rgb"], C32) >= PSNR_MIN
