@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--assets", type=int, default=N_ASSETS, help="fewer assets: a smaller case for profiling")
     ap.add_argument("--instances", type=int, default=N_INST, help="fewer instances: a smaller case for profiling")
+    ap.add_argument("--slots", type=int, default=4, help="server slots of the served leg (0: no served leg)")
+    ap.add_argument("--serve-requests", type=int, default=60)
     return ap.parse_args()
 
 
@@ -291,12 +293,16 @@ def main():
     t0 = time.perf_counter()
     for s in range(e2e_steps):
         ctx.set_instances(inst)
-        ctx.select(cams[frame_ids[s % len(frame_ids)]], args.tau)
+        ctx.select(cams[timed_ids[s % len(timed_ids)]], args.tau)
         ctx.render_host(host_rgb)
     e2e_s = time.perf_counter() - t0
     e2e_val = world * e2e_steps / max_over_ranks(e2e_s, world)
     h2d = inst.n * 256
     d2h = WIDTH * HEIGHT * 3 * 4
+
+    served = None
+    if args.slots > 0:
+        served = serve_leg(ctx, inst, cams, timed_ids, args.tau, args.slots, args.serve_requests, value)
 
     peaks, peak_kind = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
@@ -320,6 +326,7 @@ def main():
                        "per-frame gathers of the selected Gaussians exceed the 129 MB L2)"},
             "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "served": served,
             "gpu_launches": int(launches),
             "stages_ms": stage_ms,
             "frame_mean": {k: int(round(v)) for k, v in fs.items()},
@@ -332,6 +339,69 @@ def main():
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _wait(ctx, ticket):
+    r = None
+    while r is None:
+        r = ctx.poll(ticket, 100_000)
+    return r[0]
+
+
+def serve_leg(ctx, inst, cams, frame_ids, tau, slots, n_req, plain_fps):
+    """The same walk frames as requests to the library's server (v3dg_submit / v3dg_poll), with
+    host buffers like the e2e leg: instances in, image back into pinned host memory.
+
+    closed: `slots` requests always in flight; frames/s over the whole run and per-request latency
+    (submit -> done).  poisson: open-loop Poisson arrivals at 50% and 90% of the closed-loop rate;
+    latency percentiles and the rate achieved."""
+    ctx.server_start(slots)
+    cam_of = lambda k: cams[frame_ids[k % len(frame_ids)]]
+    for t in [ctx.submit(inst, cam_of(k), tau) for k in range(2 * slots)]:   # slots grow their buffers
+        _wait(ctx, t)
+    # closed loop
+    lat, t0 = [], time.perf_counter()
+    inflight = [ctx.submit(inst, cam_of(k), tau) for k in range(min(slots, n_req))]
+    nxt = len(inflight)
+    while inflight:
+        rec = _wait(ctx, inflight.pop(0))
+        lat.append(rec["done_ms"] - rec["submit_ms"])
+        if nxt < n_req:
+            inflight.append(ctx.submit(inst, cam_of(nxt), tau))
+            nxt += 1
+    closed_s = time.perf_counter() - t0
+    closed_fps = n_req / closed_s
+    out = {"slots": slots, "requests": n_req, "frames": "the timed walk frames, 1000 instances, 1080p, host buffers",
+           "closed": {"value": closed_fps, "unit": "frames/s", "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "vs_plain_device": closed_fps / plain_fps},
+           "poisson": []}
+    rng = np.random.default_rng(7)
+    for load in (0.5, 0.9):
+        rate = load * closed_fps
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+        pending, lat = [], []
+        t0 = time.perf_counter()
+        k = 0
+        while k < n_req or pending:
+            now = time.perf_counter() - t0
+            while k < n_req and arrivals[k] <= now:
+                pending.append(ctx.submit(inst, cam_of(k), tau))
+                k += 1
+            still = []
+            for t in pending:
+                r = ctx.poll(t, 0)
+                if r is None:
+                    still.append(t)
+                else:
+                    lat.append(r[0]["done_ms"] - r[0]["submit_ms"])
+            pending = still
+            if pending or k < n_req:
+                time.sleep(0.0005)
+        span = time.perf_counter() - t0
+        out["poisson"].append({"rate": rate, "achieved": n_req / span, "p50_ms": float(np.percentile(lat, 50)),
+                               "p99_ms": float(np.percentile(lat, 99))})
+    ctx.server_stop()
+    return out
 
 
 # FP32 lanes of the GB300 (152 SMs x 128) at the maximum SM clock: the issue peak of the blend

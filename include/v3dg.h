@@ -12,7 +12,8 @@
  *  - All work is enqueued on the context's stream (v3dg_set_stream; default: the legacy stream).
  *    Device memory the library needs comes from the allocator given to v3dg_create (e.g. a
  *    PyTorch caching allocator) or, when none is given, from cudaMalloc.
- *  - One context per host thread; a context is not thread-safe.
+ *  - One context per host thread; a context is not thread-safe, except v3dg_submit and v3dg_poll,
+ *    which any thread may call while a server runs.
  *  - There is no CPU fallback: without a usable CUDA device v3dg_create returns V3DG_ECUDA.
  */
 #ifndef V3DG_H
@@ -210,6 +211,64 @@ v3dg_status v3dg_sort_pairs(v3dg_ctx* ctx, uint32_t* keys, uint32_t* vals, uint6
  *    whose work overlaps on the GPU race with each other. */
 v3dg_status v3dg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, uint64_t n, int begin_bit, int end_bit,
                                     void* cuda_stream);
+
+/* ---------------------------------------------------------------- serving
+ * Many independent frames (each its own scene, camera and tolerance) rendered concurrently for
+ * interactive or batch clients.  The paper measures one viewer at a time (Sec. 5); serving
+ * repeats its per-frame path (select, Sec. 3.4, then splat, Sec. 2.1) once per request.
+ *
+ * v3dg_server_start starts `slots` workers (1..64) on the context's device.  Each worker owns its
+ * own stream and frame buffers (from cudaMalloc: the context's allocator is only ever called from
+ * the thread that owns the context) and shares the loaded assets (load them all first).  Requests wait in arrival order; a free worker takes
+ * the next one when the device-memory estimates of the requests in flight plus its own fit
+ * `hbm_budget` bytes (0: no limit; a request is always admitted when none is in flight), so
+ * requests overlap on the GPU as soon as they arrive.  Each frame is checked and re-run with
+ * larger buffers on overflow, as v3dg_render does with V3DG_OPT_SYNC_CHECK.  While a server runs,
+ * v3dg_set_option and v3dg_load_hierarchy return V3DG_EBUSY.  Status EBUSY if a server already
+ * runs, ENOTFOUND if no asset is loaded. */
+v3dg_status v3dg_server_start(v3dg_ctx* ctx, int slots, uint64_t hbm_budget);
+
+/* Finish every queued request, then stop the workers and free their buffers (results not yet
+ * polled are dropped).  v3dg_destroy does this too. */
+v3dg_status v3dg_server_stop(v3dg_ctx* ctx);
+
+/* One frame request.  Instance arrays are host pointers as in v3dg_set_instances and camera /
+ * tau_px are as in v3dg_select; all are copied by v3dg_submit.  rgb_out (h*w*3 float32) and t_out
+ * (h*w float32, or NULL) are host memory when out_on_device == 0 (pinned memory copies faster),
+ * else device memory; they are written before the request completes and must stay valid until
+ * v3dg_poll reports it. */
+typedef struct {
+  uint32_t n_instances;
+  int32_t out_on_device;
+  const uint32_t* asset_id;
+  const double* rot;
+  const double* trans;
+  const double* scale;
+  v3dg_camera camera;
+  float tau_px;
+  float* rgb_out;
+  float* t_out;
+} v3dg_request;
+
+/* Completion record.  Times are milliseconds on the server's steady clock since it started. */
+typedef struct {
+  v3dg_status status;  /* the frame's own status (V3DG_OK, V3DG_ETIMEOUT, V3DG_ECUDA, ...) */
+  uint32_t reserved;
+  double submit_ms, start_ms, done_ms;
+  uint64_t visible;    /* visible Gaussians of the frame */
+  uint64_t pairs;      /* (tile, Gaussian) pairs of the frame */
+} v3dg_result;
+
+/* Queue a request; *ticket receives its id (1, 2, ...).  Validation errors are returned here
+ * (EINVAL; ENOTFOUND for an unknown asset id or when no server runs; EBUSY while it stops) and
+ * nothing is queued then.  v3dg_submit and v3dg_poll may be called from any thread and leave
+ * v3dg_last_error unchanged; they must not overlap v3dg_server_stop or v3dg_destroy. */
+v3dg_status v3dg_submit(v3dg_ctx* ctx, const v3dg_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_us microseconds for request `ticket`.  V3DG_OK: *out holds its completion
+ * record and the ticket is forgotten; V3DG_EBUSY: not done yet (poll again); V3DG_ENOTFOUND: a
+ * ticket that was never issued or was already reported. */
+v3dg_status v3dg_poll(v3dg_ctx* ctx, uint64_t ticket, uint32_t timeout_us, v3dg_result* out);
 
 #ifdef __cplusplus
 }

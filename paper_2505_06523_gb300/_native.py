@@ -60,6 +60,19 @@ class v3dg_stats(ctypes.Structure):
                 ("blend_evals", ctypes.c_uint64), ("blend_contribs", ctypes.c_uint64)]
 
 
+class v3dg_request(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_uint32), ("out_on_device", ctypes.c_int32), ("asset_id", ctypes.c_void_p),
+                ("rot", ctypes.c_void_p), ("trans", ctypes.c_void_p), ("scale", ctypes.c_void_p),
+                ("camera", v3dg_camera), ("tau_px", ctypes.c_float), ("rgb_out", ctypes.c_void_p),
+                ("t_out", ctypes.c_void_p)]
+
+
+class v3dg_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_uint32), ("submit_ms", ctypes.c_double),
+                ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double), ("visible", ctypes.c_uint64),
+                ("pairs", ctypes.c_uint64)]
+
+
 _P = ctypes.c_void_p
 _U32 = ctypes.c_uint32
 _U64 = ctypes.c_uint64
@@ -86,6 +99,10 @@ SIGNATURES = {
     "v3dg_stage_times": (_I32, [_P, _P, _I32, ctypes.POINTER(_U64)]),
     "v3dg_sort_pairs": (_I32, [_P, _P, _P, _U64, _I32, _I32]),
     "v3dg_sort_pairs_noalloc": (_I32, [_P, _P, _U64, _I32, _I32, _P]),
+    "v3dg_server_start": (_I32, [_P, _I32, _U64]),
+    "v3dg_server_stop": (_I32, [_P]),
+    "v3dg_submit": (_I32, [_P, ctypes.POINTER(v3dg_request), ctypes.POINTER(_U64)]),
+    "v3dg_poll": (_I32, [_P, _U64, _U32, ctypes.POINTER(v3dg_result)]),
 }
 
 _lib = None
@@ -212,3 +229,27 @@ def v3dg_sort_pairs_noalloc(keys_ptr: int, vals_ptr: int, n: int, begin_bit: int
                                        _P(stream_ptr) if stream_ptr else None)
     if st != V3DG_OK:
         raise V3dgError(st, f"v3dg_sort_pairs_noalloc(n={n}, bits [{begin_bit}, {end_bit}))")
+
+
+def v3dg_server_start(ctx, slots: int, hbm_budget: int = 0) -> None:
+    _check(ctx, lib().v3dg_server_start(ctx, slots, hbm_budget))
+
+
+def v3dg_server_stop(ctx) -> None:
+    _check(ctx, lib().v3dg_server_stop(ctx))
+
+
+def v3dg_submit(ctx, req: v3dg_request) -> int:
+    t = _U64()
+    _check(ctx, lib().v3dg_submit(ctx, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def v3dg_poll(ctx, ticket: int, timeout_us: int) -> dict | None:
+    """The completion record of `ticket`, or None while it is not done (V3DG_EBUSY)."""
+    r = v3dg_result()
+    st = lib().v3dg_poll(ctx, ticket, timeout_us, ctypes.byref(r))
+    if st == V3DG_EBUSY:
+        return None
+    _check(ctx, st)
+    return {f: getattr(r, f) for f, _ in v3dg_result._fields_ if f != "reserved"}

@@ -88,6 +88,7 @@ class Context:
         self.stream = torch.cuda.current_stream(self.device)
         N.v3dg_set_stream(self.ctx, self.stream.cuda_stream)
         self.cam = None
+        self._requests = {}   # ticket -> output buffers kept alive until poll reports it
 
     # -- lifetime
     def close(self):
@@ -193,6 +194,45 @@ class Context:
         return out
 
     # -- the sort on its own
+    # -- serving
+    def server_start(self, slots: int = 4, hbm_budget: int = 0):
+        N.v3dg_server_start(self.ctx, int(slots), int(hbm_budget))
+        self._requests = {}
+
+    def server_stop(self):
+        N.v3dg_server_stop(self.ctx)
+        self._requests = {}
+
+    def submit(self, inst, cam, tau_px: float, want_T: bool = False, pinned: bool = True) -> int:
+        """Queue one frame (its own instances, camera and tolerance); returns its ticket.  The image
+        is written into host memory that this object keeps until ``poll`` reports the request."""
+        torch = self._torch
+        n = int(len(inst.asset))
+        a = np.ascontiguousarray(inst.asset, np.uint32)
+        r = np.ascontiguousarray(np.asarray(inst.rot, np.float64).reshape(n, 9))
+        t = np.ascontiguousarray(np.asarray(inst.trans, np.float64).reshape(n, 3))
+        s = np.ascontiguousarray(inst.scale, np.float64)
+        h, w = int(cam.height), int(cam.width)
+        rgb = torch.empty((h, w, 3), dtype=torch.float32, pin_memory=pinned)
+        T = torch.empty((h, w), dtype=torch.float32, pin_memory=pinned) if want_T else None
+        req = N.v3dg_request(n_instances=n, out_on_device=0, asset_id=a.ctypes.data, rot=r.ctypes.data,
+                             trans=t.ctypes.data, scale=s.ctypes.data, camera=camera_struct(cam),
+                             tau_px=float(tau_px), rgb_out=rgb.data_ptr(),
+                             t_out=T.data_ptr() if T is not None else None)
+        ticket = N.v3dg_submit(self.ctx, req)
+        self._requests[ticket] = (rgb, T)
+        return ticket
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """(record, rgb (h, w, 3) numpy, T or None) once request `ticket` is done, else None."""
+        rec = N.v3dg_poll(self.ctx, int(ticket), int(timeout_us))
+        if rec is None:
+            return None
+        rgb, T = self._requests.pop(ticket)
+        if rec["status"] != N.V3DG_OK:
+            raise N.V3dgError(rec["status"], f"request {ticket} failed")
+        return rec, rgb.numpy(), (T.numpy() if T is not None else None)
+
     def sort_pairs(self, keys, vals, begin_bit: int = 0, end_bit: int = 32):
         """In-place stable radix sort of int32/uint32 CUDA tensors keys, vals (same length)."""
         assert keys.is_cuda and vals.is_cuda and keys.numel() == vals.numel()

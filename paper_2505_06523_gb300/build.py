@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, verbose or ptxas_info), SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *objs]
+    cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

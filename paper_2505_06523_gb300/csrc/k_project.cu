@@ -18,11 +18,6 @@ namespace {
 
 constexpr int kProjThreads = 256;
 
-// One colour value (opacity or SH) of Gaussian j from a cluster block's colour section.
-__device__ __forceinline__ float ld_color(const unsigned char* col, bool half, int plane, int j) {
-  return half ? __half2float(reinterpret_cast<const __half*>(col)[plane * kSlots + j])
-              : reinterpret_cast<const float*>(col)[plane * kSlots + j];
-}
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kMinOpacity = 0.0039215689f;  // smallest float >= 1/255 (0x3b808081)
 
@@ -69,6 +64,162 @@ k_noderef(const uint2* __restrict__ list, uint32_t cap, const InstFrame* __restr
   }
 }
 
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(__half x) { return __half2float(x); }
+
+// Projects the (<= 64) Gaussians of render-list entry ci, two per lane; returns how many of this
+// lane's Gaussians are visible.  TC is the colour storage type (float or __half): the colour
+// pointer is typed and restrict-qualified so that all of a Gaussian's loads can be in flight at
+// once.
+template <typename TC>
+__device__ __forceinline__ uint32_t project_node(int lane, uint32_t ci, uint32_t cnt, const InstFrame& I,
+                                                 const CamConst& cam, const float4 bc, const float4 r0,
+                                                 const float4 r1, int nsh, const float* __restrict__ at,
+                                                 const TC* __restrict__ col, float4* __restrict__ rec,
+                                                 uint2* __restrict__ rect, uint32_t* __restrict__ keys) {
+  const bool comp = r1.w != 0.f;
+  constexpr size_t st = kSlots;   // values between planes
+  uint32_t nvis = 0;
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t j = lane + 32 * h;
+    const size_t slot = size_t(ci) * kSlots + j;
+    if (j >= cnt) {
+      keys[slot] = 0xFFFFFFFFu;
+      continue;
+    }
+    const float mx = at[kX * st + j], my = at[kY * st + j], mz = at[kZ * st + j];
+    const float op = to_f32(col[kOpacity * st + j]);
+    // float32 depth key: ((M20 x + M21 y) + M22 z) + M23, every step rounded (no fusion)
+    const float z32 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(I.m[8], mx), __fmul_rn(I.m[9], my)),
+                                          __fmul_rn(I.m[10], mz)), I.m[11]);
+    bool vis = (z32 >= cam.near_z) && (op >= kMinOpacity);
+    // offsets from the node centre in view space
+    const float dx0 = mx - bc.x, dy0 = my - bc.y, dz0 = mz - bc.z;
+    const float a = fmaf(I.m[0], dx0, fmaf(I.m[1], dy0, I.m[2] * dz0));
+    const float b = fmaf(I.m[4], dx0, fmaf(I.m[5], dy0, I.m[6] * dz0));
+    const float c = fmaf(I.m[8], dx0, fmaf(I.m[9], dy0, I.m[10] * dz0));
+    const float z = r1.z + c;
+    float corr_u, corr_v, xz, yz;
+    if (comp) {
+      const float eu = (a - r1.x * c) / z, ev = (b - r1.y * c) / z;
+      corr_u = cam.fx * eu;
+      corr_v = cam.fy * ev;
+      xz = r1.x + eu;
+      yz = r1.y + ev;
+    } else {
+      xz = (r1.x + a) / z;
+      yz = (r1.y + b) / z;
+      corr_u = cam.fx * xz;
+      corr_v = cam.fy * yz;
+    }
+    // covariance factor A = M3 R(q) diag(exp(log-scale)): Sigma_v = A A^T
+    float qw = at[kQw * st + j], qx = at[kQx * st + j], qy = at[kQy * st + j], qz = at[kQz * st + j];
+    const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
+    const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
+    const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
+    const float s0 = expf(at[kLs0 * st + j]), s1 = expf(at[kLs1 * st + j]), s2 = expf(at[kLs2 * st + j]);
+    float Am[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float m0 = I.m[4 * r], m1 = I.m[4 * r + 1], m2 = I.m[4 * r + 2];
+      Am[r][0] = fmaf(m0, R00, fmaf(m1, R10, m2 * R20)) * s0;
+      Am[r][1] = fmaf(m0, R01, fmaf(m1, R11, m2 * R21)) * s1;
+      Am[r][2] = fmaf(m0, R02, fmaf(m1, R12, m2 * R22)) * s2;
+    }
+    // EWA Jacobian at the mean, clamped to 1.3x the half field of view
+    const float rz = 1.f / z;
+    const float J00 = cam.fx * rz, J11 = cam.fy * rz;
+    const float J02 = -cam.fx * fminf(fmaxf(xz, -cam.limx), cam.limx) * rz;
+    const float J12 = -cam.fy * fminf(fmaxf(yz, -cam.limy), cam.limy) * rz;
+    const float T00 = fmaf(J00, Am[0][0], J02 * Am[2][0]), T01 = fmaf(J00, Am[0][1], J02 * Am[2][1]),
+                T02 = fmaf(J00, Am[0][2], J02 * Am[2][2]);
+    const float T10 = fmaf(J11, Am[1][0], J12 * Am[2][0]), T11 = fmaf(J11, Am[1][1], J12 * Am[2][1]),
+                T12 = fmaf(J11, Am[1][2], J12 * Am[2][2]);
+    const float ca = fmaf(T00, T00, fmaf(T01, T01, T02 * T02));
+    const float cb = fmaf(T00, T10, fmaf(T01, T11, T02 * T12));
+    const float cc = fmaf(T10, T10, fmaf(T11, T11, T12 * T12));
+    // det(T T^T) as the sum of squared 2x2 minors (Cauchy-Binet): never negative
+    const float m01 = fmaf(T00, T11, -T01 * T10), m02 = fmaf(T00, T12, -T02 * T10), m12 = fmaf(T01, T12, -T02 * T11);
+    const float det = fmaf(m01, m01, fmaf(m02, m02, m12 * m12));
+    float ia, ib, ic;
+    if (det >= 1e-12f) {
+      const float id = 1.f / det;
+      ia = cc * id;
+      ib = -cb * id;
+      ic = ca * id;
+    } else {  // near-singular: form and invert Sigma_2D in FP64
+      const double d00 = double(T00), d01 = double(T01), d02 = double(T02);
+      const double d10 = double(T10), d11 = double(T11), d12 = double(T12);
+      const double e01 = d00 * d11 - d01 * d10, e02 = d00 * d12 - d02 * d10, e12 = d01 * d12 - d02 * d11;
+      const double dd = e01 * e01 + e02 * e02 + e12 * e12;
+      if (!(dd > 0.0)) vis = false;
+      const double idd = 1.0 / dd;
+      ia = float((d10 * d10 + d11 * d11 + d12 * d12) * idd);
+      ib = float(-(d00 * d10 + d01 * d11 + d02 * d12) * idd);
+      ic = float((d00 * d00 + d01 * d01 + d02 * d02) * idd);
+    }
+    // alpha >= 1/255 ellipse: q <= k = 2 ln(255 o); its box half-widths sqrt(k Sigma_xx), sqrt(k Sigma_yy)
+    const float kq = 2.f * logf(255.f * op);
+    const float hx = sqrtf(fmaxf(kq * ca, 0.f)), hy = sqrtf(fmaxf(kq * cc, 0.f));
+    const float u = r0.x + (r0.y + corr_u), v = r0.z + (r0.w + corr_v);
+    float x0 = fmaxf(ceilf(u - hx - 0.5f), 0.f), x1 = fminf(floorf(u + hx - 0.5f), float(cam.width - 1));
+    float y0 = fmaxf(ceilf(v - hy - 0.5f), 0.f), y1 = fminf(floorf(v + hy - 0.5f), float(cam.height - 1));
+    vis = vis && (x0 <= x1) && (y0 <= y1) && isfinite(u) && isfinite(v);
+    if (!vis) {
+      keys[slot] = 0xFFFFFFFFu;
+      continue;
+    }
+    const int tx0 = int(x0) >> 4, tx1 = int(x1) >> 4, ty0 = int(y0) >> 4, ty1 = int(y1) >> 4;
+    // mean relative to the first tile's pixel origin (exact subtraction of the integer part)
+    const float u_rel = (r0.x - float(16 * tx0)) + (r0.y + corr_u);
+    const float v_rel = (r0.z - float(16 * ty0)) + (r0.w + corr_v);
+    // colour: SH in the asset frame along the direction from the camera centre
+    float dx = mx - I.cam_a[0], dy = my - I.cam_a[1], dz = mz - I.cam_a[2];
+    const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= dn; dy *= dn; dz *= dn;
+    float Y[kMaxShCoeffs];
+    Y[0] = kY0;
+    if (nsh > 1) {
+      Y[1] = -kY1 * dy; Y[2] = kY1 * dz; Y[3] = -kY1 * dx;
+    }
+    if (nsh > 4) {
+      const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+      Y[4] = kY2a * dx * dy; Y[5] = -kY2a * dy * dz; Y[6] = kY2b * (2.f * zz - xx - yy);
+      Y[7] = -kY2a * dx * dz; Y[8] = kY2c * (xx - yy);
+      if (nsh > 9) {
+        Y[9] = -kY3a * dy * (3.f * xx - yy); Y[10] = kY3b * dx * dy * dz;
+        Y[11] = -kY3c * dy * (4.f * zz - xx - yy); Y[12] = kY3d * dz * (2.f * zz - 3.f * xx - 3.f * yy);
+        Y[13] = -kY3c * dx * (4.f * zz - xx - yy); Y[14] = kY3e * dz * (xx - yy);
+        Y[15] = -kY3a * dx * (xx - 3.f * yy);
+      }
+    }
+    float rgb[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxShCoeffs; ++k)
+        if (k < nsh) acc = fmaf(Y[k], to_f32(col[(kSh0 + 3 * k + ch) * st + j]), acc);
+      rgb[ch] = fmaxf(acc + 0.5f, 0.f);
+    }
+    const uint32_t origin = uint32_t(tx0) | (uint32_t(ty0) << 16);
+    float4* rp = rec + 3 * slot;
+    rp[0] = make_float4(u_rel, v_rel, -0.5f * kLog2e * ia, -kLog2e * ib);
+    rp[1] = make_float4(-0.5f * kLog2e * ic, log2f(op), rgb[0], rgb[1]);
+    rp[2] = make_float4(rgb[2], __uint_as_float(origin), __uint_as_float(uint32_t(x0) | (uint32_t(x1) << 16)),
+                        __uint_as_float(uint32_t(y0) | (uint32_t(y1) << 16)));
+    rect[slot] = make_uint2(uint32_t(tx0) | (uint32_t(tx1) << 16), uint32_t(ty0) | (uint32_t(ty1) << 16));
+    keys[slot] = __float_as_uint(z32);
+    ++nvis;
+  }
+  return nvis;
+}
+
+// kFormats: bit 0 = float32 colour planes occur, bit 1 = float16 ones occur.
+template <int kFormats>
 __global__ void __launch_bounds__(kProjThreads)
 k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* __restrict__ inst,
           const AssetDev* __restrict__ assets, CamConst cam, const float4* __restrict__ ref,
@@ -87,148 +238,15 @@ k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* _
     const uint32_t cnt = A.count[node];
     const float4 bc = A.bound[node];
     const float4 r0 = ref[2 * ci], r1 = ref[2 * ci + 1];
-    const bool comp = r1.w != 0.f;
     const unsigned char* blk = A.attr + size_t(node) * A.stride;
-    const float* __restrict__ at = reinterpret_cast<const float*>(blk);   // geometry planes
-    const unsigned char* col = blk + size_t(kGeoPlanes) * kSlots * 4;     // colour planes
-    const bool half = A.half_color != 0;
-    constexpr size_t st = kSlots;   // values between planes
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t j = lane + 32 * h;
-      const size_t slot = size_t(ci) * kSlots + j;
-      if (j >= cnt) {
-        keys[slot] = 0xFFFFFFFFu;
-        continue;
-      }
-      const float mx = at[kX * st + j], my = at[kY * st + j], mz = at[kZ * st + j];
-      const float op = ld_color(col, half, kOpacity, int(j));
-      // float32 depth key: ((M20 x + M21 y) + M22 z) + M23, every step rounded (no fusion)
-      const float z32 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(I.m[8], mx), __fmul_rn(I.m[9], my)),
-                                            __fmul_rn(I.m[10], mz)), I.m[11]);
-      bool vis = (z32 >= cam.near_z) && (op >= kMinOpacity);
-      // offsets from the node centre in view space
-      const float dx0 = mx - bc.x, dy0 = my - bc.y, dz0 = mz - bc.z;
-      const float a = fmaf(I.m[0], dx0, fmaf(I.m[1], dy0, I.m[2] * dz0));
-      const float b = fmaf(I.m[4], dx0, fmaf(I.m[5], dy0, I.m[6] * dz0));
-      const float c = fmaf(I.m[8], dx0, fmaf(I.m[9], dy0, I.m[10] * dz0));
-      const float z = r1.z + c;
-      float corr_u, corr_v, xz, yz;
-      if (comp) {
-        const float eu = (a - r1.x * c) / z, ev = (b - r1.y * c) / z;
-        corr_u = cam.fx * eu;
-        corr_v = cam.fy * ev;
-        xz = r1.x + eu;
-        yz = r1.y + ev;
-      } else {
-        xz = (r1.x + a) / z;
-        yz = (r1.y + b) / z;
-        corr_u = cam.fx * xz;
-        corr_v = cam.fy * yz;
-      }
-      // covariance factor A = M3 R(q) diag(exp(log-scale)): Sigma_v = A A^T
-      float qw = at[kQw * st + j], qx = at[kQx * st + j], qy = at[kQy * st + j], qz = at[kQz * st + j];
-      const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-      qw *= qn; qx *= qn; qy *= qn; qz *= qn;
-      const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
-      const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
-      const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
-      const float s0 = expf(at[kLs0 * st + j]), s1 = expf(at[kLs1 * st + j]), s2 = expf(at[kLs2 * st + j]);
-      float Am[3][3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float m0 = I.m[4 * r], m1 = I.m[4 * r + 1], m2 = I.m[4 * r + 2];
-        Am[r][0] = fmaf(m0, R00, fmaf(m1, R10, m2 * R20)) * s0;
-        Am[r][1] = fmaf(m0, R01, fmaf(m1, R11, m2 * R21)) * s1;
-        Am[r][2] = fmaf(m0, R02, fmaf(m1, R12, m2 * R22)) * s2;
-      }
-      // EWA Jacobian at the mean, clamped to 1.3x the half field of view
-      const float rz = 1.f / z;
-      const float J00 = cam.fx * rz, J11 = cam.fy * rz;
-      const float J02 = -cam.fx * fminf(fmaxf(xz, -cam.limx), cam.limx) * rz;
-      const float J12 = -cam.fy * fminf(fmaxf(yz, -cam.limy), cam.limy) * rz;
-      const float T00 = fmaf(J00, Am[0][0], J02 * Am[2][0]), T01 = fmaf(J00, Am[0][1], J02 * Am[2][1]),
-                  T02 = fmaf(J00, Am[0][2], J02 * Am[2][2]);
-      const float T10 = fmaf(J11, Am[1][0], J12 * Am[2][0]), T11 = fmaf(J11, Am[1][1], J12 * Am[2][1]),
-                  T12 = fmaf(J11, Am[1][2], J12 * Am[2][2]);
-      const float ca = fmaf(T00, T00, fmaf(T01, T01, T02 * T02));
-      const float cb = fmaf(T00, T10, fmaf(T01, T11, T02 * T12));
-      const float cc = fmaf(T10, T10, fmaf(T11, T11, T12 * T12));
-      // det(T T^T) as the sum of squared 2x2 minors (Cauchy-Binet): never negative
-      const float m01 = fmaf(T00, T11, -T01 * T10), m02 = fmaf(T00, T12, -T02 * T10), m12 = fmaf(T01, T12, -T02 * T11);
-      const float det = fmaf(m01, m01, fmaf(m02, m02, m12 * m12));
-      float ia, ib, ic;
-      if (det >= 1e-12f) {
-        const float id = 1.f / det;
-        ia = cc * id;
-        ib = -cb * id;
-        ic = ca * id;
-      } else {  // near-singular: form and invert Sigma_2D in FP64
-        const double d00 = double(T00), d01 = double(T01), d02 = double(T02);
-        const double d10 = double(T10), d11 = double(T11), d12 = double(T12);
-        const double e01 = d00 * d11 - d01 * d10, e02 = d00 * d12 - d02 * d10, e12 = d01 * d12 - d02 * d11;
-        const double dd = e01 * e01 + e02 * e02 + e12 * e12;
-        if (!(dd > 0.0)) vis = false;
-        const double idd = 1.0 / dd;
-        ia = float((d10 * d10 + d11 * d11 + d12 * d12) * idd);
-        ib = float(-(d00 * d10 + d01 * d11 + d02 * d12) * idd);
-        ic = float((d00 * d00 + d01 * d01 + d02 * d02) * idd);
-      }
-      // alpha >= 1/255 ellipse: q <= k = 2 ln(255 o); its box half-widths sqrt(k Sigma_xx), sqrt(k Sigma_yy)
-      const float kq = 2.f * logf(255.f * op);
-      const float hx = sqrtf(fmaxf(kq * ca, 0.f)), hy = sqrtf(fmaxf(kq * cc, 0.f));
-      const float u = r0.x + (r0.y + corr_u), v = r0.z + (r0.w + corr_v);
-      float x0 = fmaxf(ceilf(u - hx - 0.5f), 0.f), x1 = fminf(floorf(u + hx - 0.5f), float(cam.width - 1));
-      float y0 = fmaxf(ceilf(v - hy - 0.5f), 0.f), y1 = fminf(floorf(v + hy - 0.5f), float(cam.height - 1));
-      vis = vis && (x0 <= x1) && (y0 <= y1) && isfinite(u) && isfinite(v);
-      if (!vis) {
-        keys[slot] = 0xFFFFFFFFu;
-        continue;
-      }
-      const int tx0 = int(x0) >> 4, tx1 = int(x1) >> 4, ty0 = int(y0) >> 4, ty1 = int(y1) >> 4;
-      // mean relative to the first tile's pixel origin (exact subtraction of the integer part)
-      const float u_rel = (r0.x - float(16 * tx0)) + (r0.y + corr_u);
-      const float v_rel = (r0.z - float(16 * ty0)) + (r0.w + corr_v);
-      // colour: SH in the asset frame along the direction from the camera centre
-      float dx = mx - I.cam_a[0], dy = my - I.cam_a[1], dz = mz - I.cam_a[2];
-      const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
-      dx *= dn; dy *= dn; dz *= dn;
-      float Y[kMaxShCoeffs];
-      const int nsh = A.sh_coeffs;
-      Y[0] = kY0;
-      if (nsh > 1) {
-        Y[1] = -kY1 * dy; Y[2] = kY1 * dz; Y[3] = -kY1 * dx;
-      }
-      if (nsh > 4) {
-        const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
-        Y[4] = kY2a * dx * dy; Y[5] = -kY2a * dy * dz; Y[6] = kY2b * (2.f * zz - xx - yy);
-        Y[7] = -kY2a * dx * dz; Y[8] = kY2c * (xx - yy);
-        if (nsh > 9) {
-          Y[9] = -kY3a * dy * (3.f * xx - yy); Y[10] = kY3b * dx * dy * dz;
-          Y[11] = -kY3c * dy * (4.f * zz - xx - yy); Y[12] = kY3d * dz * (2.f * zz - 3.f * xx - 3.f * yy);
-          Y[13] = -kY3c * dx * (4.f * zz - xx - yy); Y[14] = kY3e * dz * (xx - yy);
-          Y[15] = -kY3a * dx * (xx - 3.f * yy);
-        }
-      }
-      float rgb[3];
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < kMaxShCoeffs; ++k)
-          if (k < nsh) acc = fmaf(Y[k], ld_color(col, half, kSh0 + 3 * k + ch, int(j)), acc);
-        rgb[ch] = fmaxf(acc + 0.5f, 0.f);
-      }
-      const uint32_t origin = uint32_t(tx0) | (uint32_t(ty0) << 16);
-      float4* rp = rec + 3 * slot;
-      rp[0] = make_float4(u_rel, v_rel, -0.5f * kLog2e * ia, -kLog2e * ib);
-      rp[1] = make_float4(-0.5f * kLog2e * ic, log2f(op), rgb[0], rgb[1]);
-      rp[2] = make_float4(rgb[2], __uint_as_float(origin), __uint_as_float(uint32_t(x0) | (uint32_t(x1) << 16)),
-                          __uint_as_float(uint32_t(y0) | (uint32_t(y1) << 16)));
-      rect[slot] = make_uint2(uint32_t(tx0) | (uint32_t(tx1) << 16), uint32_t(ty0) | (uint32_t(ty1) << 16));
-      keys[slot] = __float_as_uint(z32);
-      ++nvis;
-    }
+    const float* at = reinterpret_cast<const float*>(blk);    // geometry planes
+    const unsigned char* col = blk + size_t(kGeoPlanes) * kSlots * 4;   // colour planes
+    if (kFormats == 2 || (kFormats == 3 && A.half_color))
+      nvis += project_node<__half>(lane, ci, cnt, I, cam, bc, r0, r1, A.sh_coeffs, at,
+                                   reinterpret_cast<const __half*>(col), rec, rect, keys);
+    else
+      nvis += project_node<float>(lane, ci, cnt, I, cam, bc, r0, r1, A.sh_coeffs, at,
+                                  reinterpret_cast<const float*>(col), rec, rect, keys);
   }
   // one atomic per block for the visible count
 #pragma unroll
@@ -252,8 +270,14 @@ cudaError_t launch_noderef(const uint2* list, uint32_t cap, const InstFrame* ins
 
 cudaError_t launch_project(const uint2* list, uint32_t cap_nodes, const InstFrame* inst, const AssetDev* assets,
                            const CamConst& cam, const float4* ref, float4* rec, uint2* rect, uint32_t* keys,
-                           uint32_t* frame, int sm_count, cudaStream_t st) {
-  k_project<<<sm_count * 8, kProjThreads, 0, st>>>(list, cap_nodes, inst, assets, cam, ref, rec, rect, keys, frame);
+                           uint32_t* frame, int color_formats, int sm_count, cudaStream_t st) {
+  const int grid = sm_count * 8;
+  if (color_formats == 2)
+    k_project<2><<<grid, kProjThreads, 0, st>>>(list, cap_nodes, inst, assets, cam, ref, rec, rect, keys, frame);
+  else if (color_formats == 3)
+    k_project<3><<<grid, kProjThreads, 0, st>>>(list, cap_nodes, inst, assets, cam, ref, rec, rect, keys, frame);
+  else
+    k_project<1><<<grid, kProjThreads, 0, st>>>(list, cap_nodes, inst, assets, cam, ref, rec, rect, keys, frame);
   return cudaGetLastError();
 }
 

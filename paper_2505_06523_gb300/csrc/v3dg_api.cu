@@ -3,13 +3,25 @@
 // Owns the device state of one context: the uploaded bundles (Sec. 3, Fig. 2), the instance table
 // (Sec. 4.2), the per-frame FP64 set-up (camera V and instances composed into M = W [s R | t])
 // and the work buffers of the splatting stages, whose capacities grow when a frame overflows.
+// The per-frame state lives in a Pipe: the plain API drives the context's main pipe, and the
+// request server (v3dg_server_start / v3dg_submit / v3dg_poll) runs one more pipe per slot, each
+// on its own stream and host thread, over the same device-resident assets.
 // Host code is compiled with -ffp-contract=off: M is composed in a fixed operation order.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -42,16 +54,16 @@ enum { kStageSelect = 0, kStageProject, kStageDepthSort, kStageBin, kStageTileSo
 
 }  // namespace
 
-struct v3dg_ctx {
-  int device = 0;
-  int sm_count = 0;
-  cudaStream_t stream = nullptr;
-  v3dg_allocator alloc{};
-  bool has_alloc = false;
-  std::string err;
+struct Server;
 
-  std::vector<AssetHost> assets;
-  DevBuf d_assets;
+// Per-frame state of one pipeline: the instance table and camera set-up of its frames, its work
+// buffers and their capacities, frame counters and the stream its work goes to.  The context's
+// plain API drives the main pipe; each serving slot owns one more.
+struct Pipe {
+  v3dg_ctx* ctx = nullptr;
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool ctx_alloc = true;   // device memory from the context's allocator (else cudaMalloc)
 
   std::vector<uint32_t> inst_asset;
   std::vector<double> inst_rot, inst_trans, inst_scale;
@@ -72,22 +84,39 @@ struct v3dg_ctx {
   uint32_t* h_tmp = nullptr;     // pinned scratch: [0, 48) frame words of read-backs, [48, 52) blend work
 
   uint32_t cap_nodes = 0, cap_slots = 0, cap_pairs = 0, status_words = 0, cap_cut = 0;
-  DevBuf d_list, d_ref, d_keys0, d_keys1, d_vals0, d_vals1, d_rec, d_rect, d_off;
+  DevBuf d_list, d_ref, d_keys0, d_keys1, d_vals0, d_vals1, d_rec, d_rect;
   DevBuf d_pk0, d_pk1, d_pv0, d_pv1, d_ranges, d_status, d_hist, d_cut;
   DevBuf d_img, d_timg, d_sort_k, d_sort_v, d_order;
   bool depth_in1 = false, tiles_in1 = false;
   uint32_t epoch = 1;
-  uint64_t launches = 0;
+  cudaEvent_t ev[kStages + 1] = {};
+};
+
+struct v3dg_ctx {
+  int device = 0;
+  int sm_count = 0;
+  v3dg_allocator alloc{};
+  bool has_alloc = false;
+  std::vector<AssetHost> assets;
+  DevBuf d_assets;
+  std::atomic<uint64_t> launches{0};
   bool sync_check = true, stage_timing = false, count_work = false;
   uint32_t split_pairs = 16384;
   bool attr_fp16 = false;   // store opacity and SH of the next loaded assets as float16
-  unsigned long long work[2] = {0, 0};
-  cudaEvent_t ev[kStages + 1] = {};
+  Pipe main;
+  Server* server = nullptr;
 };
 
 namespace {
 
-v3dg_status fail(v3dg_ctx* c, v3dg_status s, const char* fmt, ...) {
+// Colour storage formats among the loaded assets: bit 0 float32, bit 1 float16.
+int color_formats(const v3dg_ctx* ctx) {
+  int f = 0;
+  for (const AssetHost& a : ctx->assets) f |= a.half_color ? 2 : 1;
+  return f;
+}
+
+v3dg_status fail(Pipe* c, v3dg_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -109,10 +138,10 @@ v3dg_status fail(v3dg_ctx* c, v3dg_status s, const char* fmt, ...) {
     if (s_ != V3DG_OK) return s_;                                                                  \
   } while (0)
 
-void dfree(v3dg_ctx* c, DevBuf& b) {
+void dfree(Pipe* c, DevBuf& b) {
   if (b.p) {
-    if (c->has_alloc)
-      c->alloc.free(b.p, c->alloc.user);
+    if (c->ctx->has_alloc && c->ctx_alloc)
+      c->ctx->alloc.free(b.p, c->ctx->alloc.user);
     else
       cudaFree(b.p);
   }
@@ -120,12 +149,12 @@ void dfree(v3dg_ctx* c, DevBuf& b) {
   b.bytes = 0;
 }
 
-v3dg_status dalloc(v3dg_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
+v3dg_status dalloc(Pipe* c, DevBuf& b, size_t bytes, bool zero = false) {
   if (bytes == 0) bytes = 256;
   bytes = (bytes + 255) & ~size_t(255);
   void* p = nullptr;
-  if (c->has_alloc) {
-    p = c->alloc.alloc(bytes, c->alloc.user);
+  if (c->ctx->has_alloc && c->ctx_alloc) {
+    p = c->ctx->alloc.alloc(bytes, c->ctx->alloc.user);
     if (!p) return fail(c, V3DG_ENOMEM, "allocator returned NULL for %zu bytes", bytes);
   } else {
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -141,7 +170,7 @@ v3dg_status dalloc(v3dg_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
   return V3DG_OK;
 }
 
-v3dg_status ensure(v3dg_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
+v3dg_status ensure(Pipe* c, DevBuf& b, size_t bytes, bool zero = false) {
   if (b.p && b.bytes >= bytes) return V3DG_OK;
   return dalloc(c, b, bytes, zero);
 }
@@ -151,7 +180,7 @@ T* P(const DevBuf& b) {
   return static_cast<T*>(b.p);
 }
 
-uint32_t next_epoch(v3dg_ctx* c) {
+uint32_t next_epoch(Pipe* c) {
   c->epoch = (c->epoch + 1) & 0x3FFFFFFFu;
   if (c->epoch == 0) c->epoch = 1;
   return c->epoch;
@@ -163,7 +192,7 @@ float round_up_f(double x) {
   return f;
 }
 
-v3dg_status ensure_status(v3dg_ctx* c, uint64_t words) {
+v3dg_status ensure_status(Pipe* c, uint64_t words) {
   if (words <= c->status_words && c->d_status.p) return V3DG_OK;
   if (words > 0xFFFFFFFFull) return fail(c, V3DG_EOVERFLOW, "status array too large");
   ST(dalloc(c, c->d_status, 8 * words, true));
@@ -172,7 +201,7 @@ v3dg_status ensure_status(v3dg_ctx* c, uint64_t words) {
 }
 
 // Work buffers sized by the current capacities.
-v3dg_status ensure_work(v3dg_ctx* c) {
+v3dg_status ensure_work(Pipe* c) {
   if (c->cap_nodes == 0) c->cap_nodes = kInitNodes;
   if (c->cap_pairs == 0) c->cap_pairs = kInitPairs;
   c->cap_slots = c->cap_nodes * uint32_t(kSlots);
@@ -198,7 +227,7 @@ v3dg_status ensure_work(v3dg_ctx* c) {
   return V3DG_OK;
 }
 
-SortScratch sort_scratch(v3dg_ctx* c, uint32_t* tile_counters) {
+SortScratch sort_scratch(Pipe* c, uint32_t* tile_counters) {
   SortScratch sc;
   sc.hist = P<uint32_t>(c->d_hist);
   sc.status = P<uint64_t>(c->d_status);
@@ -207,13 +236,13 @@ SortScratch sort_scratch(v3dg_ctx* c, uint32_t* tile_counters) {
   return sc;
 }
 
-void stage_event(v3dg_ctx* c, int i) {
-  if (c->stage_timing) cudaEventRecord(c->ev[i], c->stream);
+void stage_event(Pipe* c, int i) {
+  if (c->ctx->stage_timing) cudaEventRecord(c->ev[i], c->stream);
 }
 
 // ------------------------------------------------------------------ per-frame set-up (FP64, host)
 
-v3dg_status setup_frame(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
+v3dg_status setup_frame(Pipe* c, const v3dg_camera* cam, float tau_px) {
   if (!cam) return fail(c, V3DG_EINVAL, "camera is NULL");
   if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 * 16 || cam->height > 65535 * 16)
     return fail(c, V3DG_EINVAL, "bad image size %d x %d", cam->width, cam->height);
@@ -223,7 +252,7 @@ v3dg_status setup_frame(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
   for (double v : cam->world_to_cam)
     if (!std::isfinite(v)) return fail(c, V3DG_EINVAL, "non-finite world_to_cam");
   if (!(tau_px >= 0.f) || !std::isfinite(tau_px)) return fail(c, V3DG_EINVAL, "tau_px must be finite and >= 0");
-  if (c->assets.empty()) return fail(c, V3DG_ENOTFOUND, "no hierarchy loaded");
+  if (c->ctx->assets.empty()) return fail(c, V3DG_ENOTFOUND, "no hierarchy loaded");
   const uint64_t tiles = uint64_t((cam->width + kTile - 1) / kTile) * uint64_t((cam->height + kTile - 1) / kTile);
   if (tiles > (1u << 24)) return fail(c, V3DG_EINVAL, "image too large (%llu tiles)", (unsigned long long)tiles);
   const uint32_t n = uint32_t(c->inst_asset.size());
@@ -246,7 +275,7 @@ v3dg_status setup_frame(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
   k.cull_ky = float(std::sqrt(two_ln255 * (1.0 + double(k.limy) * double(k.limy))) * 1.01);
 
   uint32_t max_nodes = 0;
-  for (auto& a : c->assets) max_nodes = std::max(max_nodes, a.n_nodes);
+  for (auto& a : c->ctx->assets) max_nodes = std::max(max_nodes, a.n_nodes);
   c->node_blocks = int((max_nodes + 2047) / 2048);   // k_select covers 2048 nodes per block
   c->n_inst_frame = n;
 
@@ -286,7 +315,7 @@ v3dg_status setup_frame(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
     f.s64 = s;
     const uint32_t a = c->inst_asset[i];
     f.asset = a;
-    f.tau_f = float(double(c->assets[a].gpg) * double(tau_px) * double(tau_px));
+    f.tau_f = float(double(c->ctx->assets[a].gpg) * double(tau_px) * double(tau_px));
   }
   if (n) CU(cudaMemcpyAsync(c->d_inst.p, c->h_inst, sizeof(InstFrame) * n, cudaMemcpyHostToDevice, c->stream));
   if (!c->ev_inst) CU(cudaEventCreateWithFlags(&c->ev_inst, cudaEventDisableTiming));
@@ -294,15 +323,15 @@ v3dg_status setup_frame(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
   return V3DG_OK;
 }
 
-v3dg_status enqueue_select(v3dg_ctx* c) {
+v3dg_status enqueue_select(Pipe* c) {
   ST(ensure_work(c));
   CU(cudaMemsetAsync(c->d_frame.p, 0, sizeof(uint32_t) * kFrameWords, c->stream));
   stage_event(c, kStageSelect);
   if (c->n_inst_frame) {
-    CU(launch_select(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->d_assets), c->node_blocks, c->cc, 0,
+    CU(launch_select(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->ctx->d_assets), c->node_blocks, c->cc, 0,
                      P<uint2>(c->d_list), c->cap_nodes, P<uint32_t>(c->d_frame), 0, P<uint64_t>(c->d_status),
                      next_epoch(c), c->stream));
-    ++c->launches;
+    ++c->ctx->launches;
   }
   return V3DG_OK;
 }
@@ -317,19 +346,19 @@ __global__ void k_render_reset(uint32_t* frame, uint32_t cap_nodes) {
 
 __global__ void k_set_word(uint32_t* p, uint32_t v) { *p = v; }
 
-v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
+v3dg_status enqueue_render(Pipe* c, float* rgb, float* t_out) {
   const CamConst& k = c->cc;
   uint32_t* frame = P<uint32_t>(c->d_frame);
-  const int sm = c->sm_count;
+  const int sm = c->ctx->sm_count;
   stage_event(c, kStageProject);
   k_render_reset<<<1, kFrameWords, 0, c->stream>>>(frame, c->cap_nodes);
   CU(cudaGetLastError());
-  CU(launch_noderef(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->d_assets), k,
+  CU(launch_noderef(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->ctx->d_assets), k,
                     P<float4>(c->d_ref), frame, sm, c->stream));
-  CU(launch_project(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->d_assets), k,
-                    P<float4>(c->d_ref), P<float4>(c->d_rec), P<uint2>(c->d_rect), P<uint32_t>(c->d_keys0), frame, sm,
-                    c->stream));
-  c->launches += 3;
+  CU(launch_project(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->ctx->d_assets), k,
+                    P<float4>(c->d_ref), P<float4>(c->d_rec), P<uint2>(c->d_rect), P<uint32_t>(c->d_keys0), frame,
+                    color_formats(c->ctx), sm, c->stream));
+  c->ctx->launches += 3;
 
   stage_event(c, kStageDepthSort);
   bool in1 = false;
@@ -338,14 +367,14 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
                  frame + kSlotCount, c->cap_slots, 0, 32, true, sort_scratch(c, frame + kTileCounters + 2),
                  frame + kTimeout, c->epoch, sm, c->stream, &in1, &nl));
   next_epoch(c);
-  c->launches += nl;
+  c->ctx->launches += nl;
   c->depth_in1 = in1;
   const uint32_t* dslots = in1 ? P<uint32_t>(c->d_vals1) : P<uint32_t>(c->d_vals0);
 
   stage_event(c, kStageBin);
   CU(launch_expand(dslots, P<uint2>(c->d_rect), c->cap_slots, c->cap_pairs, k.tiles_x, P<uint32_t>(c->d_pk0),
                    P<uint32_t>(c->d_pv0), frame, 1, P<uint64_t>(c->d_status), next_epoch(c), c->stream));
-  c->launches += 2;
+  c->ctx->launches += 2;
 
   stage_event(c, kStageTileSort);
   const int n_tiles = k.tiles_x * k.tiles_y;
@@ -357,7 +386,7 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
                  frame + kPairsEff, c->cap_pairs, 0, tile_bits, false, sort_scratch(c, frame + kTileCounters + 6),
                  frame + kTimeout, c->epoch, sm, c->stream, &tin1, &nl));
   next_epoch(c);
-  c->launches += nl;
+  c->ctx->launches += nl;
   c->tiles_in1 = tin1;
   const uint32_t* tk = tin1 ? P<uint32_t>(c->d_pk1) : P<uint32_t>(c->d_pk0);
   const uint32_t* tv = tin1 ? P<uint32_t>(c->d_pv1) : P<uint32_t>(c->d_pv0);
@@ -366,17 +395,17 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
   ST(ensure(c, c->d_ranges, sizeof(uint2) * size_t(n_tiles)));
   ST(ensure(c, c->d_order, sizeof(uint32_t) * (4 * size_t(n_tiles) + 1)));
   CU(launch_ranges(tk, c->cap_pairs, frame, P<uint2>(c->d_ranges), n_tiles, sm, c->stream));
-  c->launches += 1;
+  c->ctx->launches += 1;
 
   stage_event(c, kStageBlend);
   // d_misc: [0..7] the standalone sort's words, [8..11] two 64-bit blend work counters
-  unsigned long long* work = c->count_work ? reinterpret_cast<unsigned long long*>(P<uint32_t>(c->d_misc) + 8) : nullptr;
+  unsigned long long* work = c->ctx->count_work ? reinterpret_cast<unsigned long long*>(P<uint32_t>(c->d_misc) + 8) : nullptr;
   if (work) CU(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), c->stream));
   // d_misc[12], [13]: sticky overflow / timeout flags of all frames since the last v3dg_frame_stats
   CU(launch_blend(P<uint2>(c->d_ranges), P<uint32_t>(c->d_order), frame + kTileCounters + 10, tv, P<float4>(c->d_rec),
-                  c->cap_slots, k, rgb, t_out, work, frame, P<uint32_t>(c->d_misc) + 12, c->split_pairs, sm,
+                  c->cap_slots, k, rgb, t_out, work, frame, P<uint32_t>(c->d_misc) + 12, c->ctx->split_pairs, sm,
                   c->stream));
-  c->launches += 2;
+  c->ctx->launches += 2;
   if (work)
     CU(cudaMemcpyAsync(c->h_tmp + kFrameWords, work, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   stage_event(c, kStages);
@@ -386,10 +415,10 @@ v3dg_status enqueue_render(v3dg_ctx* c, float* rgb, float* t_out) {
 }
 
 // Runs the frame; with sync checking, waits and re-runs it with larger buffers on overflow.
-v3dg_status run_frame(v3dg_ctx* c, float* rgb, float* t_out) {
+v3dg_status run_frame(Pipe* c, float* rgb, float* t_out, bool sync) {
   for (int attempt = 0; attempt < 8; ++attempt) {
     ST(enqueue_render(c, rgb, t_out));
-    if (!c->sync_check) return V3DG_OK;
+    if (!sync) return V3DG_OK;
     CU(cudaStreamSynchronize(c->stream));
     const uint32_t* f = c->h_frame;
     if (f[kTimeout]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up; frame invalid");
@@ -413,24 +442,24 @@ v3dg_status run_frame(v3dg_ctx* c, float* rgb, float* t_out) {
   return fail(c, V3DG_EOVERFLOW, "frame still overflows after growing the buffers");
 }
 
-v3dg_status sync_frame(v3dg_ctx* c) {
+v3dg_status sync_frame(Pipe* c) {
   CU(cudaStreamSynchronize(c->stream));
   if (!c->rendered) CU(cudaMemcpy(c->h_frame, c->d_frame.p, sizeof(uint32_t) * kFrameWords, cudaMemcpyDeviceToHost));
   return V3DG_OK;
 }
 
 // The cut itself (mode 1), into d_cut; returns its size.
-v3dg_status run_cut(v3dg_ctx* c, uint32_t* n_cut, uint32_t* n_gauss) {
+v3dg_status run_cut(Pipe* c, uint32_t* n_cut, uint32_t* n_gauss) {
   if (!c->selected) return fail(c, V3DG_ENOTFOUND, "no frame selected");
   if (c->cap_cut == 0) c->cap_cut = 1u << 16;
   for (int attempt = 0; attempt < 8; ++attempt) {
     ST(ensure(c, c->d_cut, sizeof(uint2) * size_t(c->cap_cut)));
     CU(cudaMemsetAsync(c->d_cutframe.p, 0, sizeof(uint32_t) * kFrameWords, c->stream));
     if (c->n_inst_frame) {
-      CU(launch_select(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->d_assets), c->node_blocks, c->cc, 1,
+      CU(launch_select(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->ctx->d_assets), c->node_blocks, c->cc, 1,
                        P<uint2>(c->d_cut), c->cap_cut, P<uint32_t>(c->d_cutframe), 0, P<uint64_t>(c->d_status),
                        next_epoch(c), c->stream));
-      ++c->launches;
+      ++c->ctx->launches;
     }
     CU(cudaMemcpyAsync(c->h_tmp, c->d_cutframe.p, sizeof(uint32_t) * kFrameWords, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -445,7 +474,7 @@ v3dg_status run_cut(v3dg_ctx* c, uint32_t* n_cut, uint32_t* n_gauss) {
   return fail(c, V3DG_EOVERFLOW, "cut read-back overflow");
 }
 
-v3dg_status validate_desc(v3dg_ctx* c, const v3dg_hierarchy_desc* d) {
+v3dg_status validate_desc(Pipe* c, const v3dg_hierarchy_desc* d) {
   if (!d) return fail(c, V3DG_EINVAL, "descriptor is NULL");
   if (d->n_gauss == 0 || d->n_nodes == 0) return fail(c, V3DG_EINVAL, "empty hierarchy");
   if (d->n_nodes > (1u << 24)) return fail(c, V3DG_EINVAL, "too many nodes (%u)", d->n_nodes);
@@ -479,6 +508,176 @@ v3dg_status validate_desc(v3dg_ctx* c, const v3dg_hierarchy_desc* d) {
   return V3DG_OK;
 }
 
+// Pinned words, frame counters and stage events of a pipe; `stream` NULL: the legacy stream (main
+// pipe) -- serving slots pass their own.
+v3dg_status pipe_init(v3dg_ctx* ctx, Pipe* c, cudaStream_t stream) {
+  c->ctx = ctx;
+  c->stream = stream;
+  if (cudaMallocHost(&c->h_frame, sizeof(uint32_t) * kFrameWords) != cudaSuccess) return V3DG_ECUDA;
+  if (cudaMallocHost(&c->h_tmp, sizeof(uint32_t) * (kFrameWords + 16)) != cudaSuccess) return V3DG_ECUDA;
+  std::memset(c->h_frame, 0, sizeof(uint32_t) * kFrameWords);
+  ST(dalloc(c, c->d_frame, sizeof(uint32_t) * kFrameWords, true));
+  ST(dalloc(c, c->d_cutframe, sizeof(uint32_t) * kFrameWords, true));
+  ST(dalloc(c, c->d_misc, sizeof(uint32_t) * 64, true));
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return V3DG_ECUDA;
+  if (c->stream) CU(cudaStreamSynchronize(c->stream));
+  return V3DG_OK;
+}
+
+void pipe_free(Pipe* c) {
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  DevBuf* bs[] = {&c->d_inst, &c->d_frame, &c->d_cutframe, &c->d_misc, &c->d_list, &c->d_ref, &c->d_keys0,
+                  &c->d_keys1, &c->d_vals0, &c->d_vals1, &c->d_rec, &c->d_rect, &c->d_pk0, &c->d_pk1,
+                  &c->d_pv0, &c->d_pv1, &c->d_ranges, &c->d_status, &c->d_hist, &c->d_cut, &c->d_img,
+                  &c->d_timg, &c->d_sort_k, &c->d_sort_v, &c->d_order};
+  for (DevBuf* b : bs) dfree(c, *b);
+  if (c->h_inst) cudaFreeHost(c->h_inst);
+  if (c->h_frame) cudaFreeHost(c->h_frame);
+  if (c->h_tmp) cudaFreeHost(c->h_tmp);
+  if (c->ev_inst) cudaEventDestroy(c->ev_inst);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  c->h_inst = nullptr;
+  c->h_frame = c->h_tmp = nullptr;
+  c->ev_inst = nullptr;
+  for (auto& e : c->ev) e = nullptr;
+}
+
+// ------------------------------------------------------------------ serving
+
+// One queued request: a copy of its scene and camera, where its image goes, and its admission
+// estimate of device memory.
+struct Request {
+  uint64_t ticket = 0;
+  std::vector<uint32_t> asset;
+  std::vector<double> rot, trans, scale;
+  v3dg_camera cam{};
+  float tau_px = 0.f;
+  float* rgb = nullptr;
+  float* t = nullptr;
+  bool out_device = false;
+  uint64_t est_bytes = 0;
+  double t_submit = 0.0;
+};
+
+struct Finished {
+  v3dg_status status = V3DG_OK;
+  double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
+  uint64_t visible = 0, pairs = 0;
+};
+
+}  // namespace
+
+// Continuous batching: each slot is a pipe with its own stream and host thread.  Requests wait in
+// arrival order; a slot takes the next one as soon as it is free and the device-memory estimates
+// of the requests in flight plus this one fit the budget (one request is always admitted), so
+// requests that arrive while others run start at once and their kernels overlap on the GPU.
+struct Server {
+  v3dg_ctx* ctx = nullptr;
+  uint64_t budget = 0;
+  std::vector<std::unique_ptr<Pipe>> slots;
+  std::vector<std::thread> threads;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request> queue;
+  std::unordered_map<uint64_t, Finished> finished;
+  std::unordered_set<uint64_t> pending;   // issued and not yet reported by v3dg_poll
+  uint64_t next_ticket = 1, in_flight = 0, active = 0;
+  bool stop = false;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double now_ms() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+// Admission estimate of a request's device memory: image and per-pixel buffers plus a share per
+// instance for its cut, records and pairs.
+uint64_t request_bytes(uint32_t n_inst, const v3dg_camera& cam) {
+  return uint64_t(cam.width) * uint64_t(cam.height) * 64u + uint64_t(n_inst) * (64u << 10);
+}
+
+v3dg_status run_request(Pipe* c, Request& rq, Finished* f) {
+  c->inst_asset.swap(rq.asset);
+  c->inst_rot.swap(rq.rot);
+  c->inst_trans.swap(rq.trans);
+  c->inst_scale.swap(rq.scale);
+  ST(setup_frame(c, &rq.cam, rq.tau_px));
+  ST(enqueue_select(c));
+  c->selected = true;
+  c->rendered = false;
+  const size_t px = size_t(rq.cam.width) * size_t(rq.cam.height);
+  float* rgb = rq.rgb;
+  float* t = rq.t;
+  if (!rq.out_device) {
+    ST(ensure(c, c->d_img, sizeof(float) * 3 * px));
+    if (t) ST(ensure(c, c->d_timg, sizeof(float) * px));
+    rgb = P<float>(c->d_img);
+    t = t ? P<float>(c->d_timg) : nullptr;
+  }
+  ST(run_frame(c, rgb, t, true));
+  if (!rq.out_device) {
+    CU(cudaMemcpyAsync(rq.rgb, c->d_img.p, sizeof(float) * 3 * px, cudaMemcpyDeviceToHost, c->stream));
+    if (rq.t) CU(cudaMemcpyAsync(rq.t, c->d_timg.p, sizeof(float) * px, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  f->visible = c->h_frame[kVisible];
+  f->pairs = c->h_frame[kPairs];
+  return V3DG_OK;
+}
+
+void slot_main(Server* sv, Pipe* p) {
+  cudaSetDevice(sv->ctx->device);
+  for (;;) {
+    Request rq;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv_work.wait(lk, [&] {
+        if (sv->queue.empty()) return sv->stop;
+        return sv->active == 0 || sv->in_flight + sv->queue.front().est_bytes <= sv->budget;
+      });
+      if (sv->queue.empty()) return;   // stopping and nothing left
+      rq = std::move(sv->queue.front());
+      sv->queue.pop_front();
+      sv->in_flight += rq.est_bytes;
+      ++sv->active;
+    }
+    Finished f;
+    f.t_submit = rq.t_submit;
+    f.t_start = sv->now_ms();
+    f.status = run_request(p, rq, &f);
+    f.t_done = sv->now_ms();
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->in_flight -= rq.est_bytes;
+      --sv->active;
+      sv->finished[rq.ticket] = f;
+    }
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
+  }
+}
+
+void server_stop(v3dg_ctx* ctx) {
+  Server* sv = ctx->server;
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv_work.notify_all();
+  for (auto& t : sv->threads) t.join();
+  for (auto& p : sv->slots) {
+    cudaStream_t st = p->stream;
+    pipe_free(p.get());
+    if (st) cudaStreamDestroy(st);
+  }
+  delete sv;
+  ctx->server = nullptr;
+}
+
 }  // namespace
 
 // ====================================================================== public ABI
@@ -495,73 +694,65 @@ v3dg_status v3dg_create(int device, const v3dg_allocator* alloc, v3dg_ctx** out)
   }
   if (device < 0 || device >= n_dev) return V3DG_EINVAL;
   if (alloc && (!alloc->alloc || !alloc->free)) return V3DG_EINVAL;
-  v3dg_ctx* c = new (std::nothrow) v3dg_ctx;
-  if (!c) return V3DG_ENOMEM;
-  c->device = device;
+  v3dg_ctx* ctx = new (std::nothrow) v3dg_ctx;
+  if (!ctx) return V3DG_ENOMEM;
+  ctx->device = device;
   if (alloc) {
-    c->alloc = *alloc;
-    c->has_alloc = true;
+    ctx->alloc = *alloc;
+    ctx->has_alloc = true;
   }
-  auto bail = [&](v3dg_status s) {
-    v3dg_destroy(c);
-    return s;
-  };
-  if (cudaSetDevice(device) != cudaSuccess) return bail(V3DG_ECUDA);
-  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return bail(V3DG_ECUDA);
-  if (cudaMallocHost(&c->h_frame, sizeof(uint32_t) * kFrameWords) != cudaSuccess) return bail(V3DG_ECUDA);
-  if (cudaMallocHost(&c->h_tmp, sizeof(uint32_t) * (kFrameWords + 16)) != cudaSuccess) return bail(V3DG_ECUDA);
-  std::memset(c->h_frame, 0, sizeof(uint32_t) * kFrameWords);
-  if (dalloc(c, c->d_frame, sizeof(uint32_t) * kFrameWords, true) != V3DG_OK) return bail(V3DG_ENOMEM);
-  if (dalloc(c, c->d_cutframe, sizeof(uint32_t) * kFrameWords, true) != V3DG_OK) return bail(V3DG_ENOMEM);
-  if (dalloc(c, c->d_misc, sizeof(uint32_t) * 64, true) != V3DG_OK) return bail(V3DG_ENOMEM);
-  for (auto& e : c->ev)
-    if (cudaEventCreate(&e) != cudaSuccess) return bail(V3DG_ECUDA);
-  *out = c;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete ctx;
+    return V3DG_ECUDA;
+  }
+  const v3dg_status st = pipe_init(ctx, &ctx->main, nullptr);
+  if (st != V3DG_OK) {
+    v3dg_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
   return V3DG_OK;
 }
 
-void v3dg_destroy(v3dg_ctx* c) {
-  if (!c) return;
-  cudaSetDevice(c->device);
+void v3dg_destroy(v3dg_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  server_stop(ctx);
+  Pipe* c = &ctx->main;
   if (c->stream) cudaStreamSynchronize(c->stream);
   cudaDeviceSynchronize();
-  for (auto& a : c->assets) {
+  for (auto& a : ctx->assets) {
     DevBuf* bs[] = {&a.own, &a.par, &a.bound, &a.sigma, &a.flags, &a.cnt, &a.attr};
     for (DevBuf* b : bs) dfree(c, *b);
   }
-  DevBuf* bs[] = {&c->d_assets, &c->d_inst, &c->d_frame, &c->d_cutframe, &c->d_misc, &c->d_list, &c->d_ref,
-                  &c->d_keys0, &c->d_keys1, &c->d_vals0, &c->d_vals1, &c->d_rec, &c->d_rect, &c->d_off, &c->d_pk0,
-                  &c->d_pk1, &c->d_pv0, &c->d_pv1, &c->d_ranges, &c->d_status, &c->d_hist, &c->d_cut, &c->d_img,
-                  &c->d_timg, &c->d_sort_k, &c->d_sort_v, &c->d_order};
-  for (DevBuf* b : bs) dfree(c, *b);
-  if (c->h_inst) cudaFreeHost(c->h_inst);
-  if (c->h_frame) cudaFreeHost(c->h_frame);
-  if (c->h_tmp) cudaFreeHost(c->h_tmp);
-  if (c->ev_inst) cudaEventDestroy(c->ev_inst);
-  for (auto& e : c->ev)
-    if (e) cudaEventDestroy(e);
-  delete c;
+  dfree(c, ctx->d_assets);
+  pipe_free(c);
+  delete ctx;
 }
 
-const char* v3dg_last_error(const v3dg_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+const char* v3dg_last_error(const v3dg_ctx* ctx) { return ctx ? ctx->main.err.c_str() : "NULL context"; }
 
-v3dg_status v3dg_set_stream(v3dg_ctx* c, void* stream) {
+v3dg_status v3dg_set_stream(v3dg_ctx* ctx, void* stream) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
   c->stream = static_cast<cudaStream_t>(stream);
   c->err.clear();
   return V3DG_OK;
 }
 
-v3dg_status v3dg_set_option(v3dg_ctx* c, int option, int64_t value) {
+v3dg_status v3dg_set_option(v3dg_ctx* ctx, int option, int64_t value) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
+  if (ctx->server) return fail(c, V3DG_EBUSY, "options cannot change while a server runs");
   switch (option) {
-    case V3DG_OPT_SYNC_CHECK: c->sync_check = value != 0; break;
-    case V3DG_OPT_STAGE_TIMING: c->stage_timing = value != 0; break;
-    case V3DG_OPT_COUNT_WORK: c->count_work = value != 0; break;
-    case V3DG_OPT_ATTR_FP16: c->attr_fp16 = value != 0; break;
+    case V3DG_OPT_SYNC_CHECK: ctx->sync_check = value != 0; break;
+    case V3DG_OPT_STAGE_TIMING: ctx->stage_timing = value != 0; break;
+    case V3DG_OPT_COUNT_WORK: ctx->count_work = value != 0; break;
+    case V3DG_OPT_ATTR_FP16: ctx->attr_fp16 = value != 0; break;
     case V3DG_OPT_SPLIT_PAIRS:
       if (value < 1 || value > 0xFFFFFFFFll) return fail(c, V3DG_EINVAL, "split threshold out of range");
-      c->split_pairs = uint32_t(value);
+      ctx->split_pairs = uint32_t(value);
       break;
     case V3DG_OPT_CAP_NODES:
       if (value < 64 || value > int64_t(kMaxNodes)) return fail(c, V3DG_EINVAL, "node capacity out of range");
@@ -577,13 +768,15 @@ v3dg_status v3dg_set_option(v3dg_ctx* c, int option, int64_t value) {
   return V3DG_OK;
 }
 
-v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint32_t* asset_id) {
+v3dg_status v3dg_load_hierarchy(v3dg_ctx* ctx, const v3dg_hierarchy_desc* d, uint32_t* asset_id) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
+  if (ctx->server) return fail(c, V3DG_EBUSY, "assets cannot be loaded while a server runs");
   ST(validate_desc(c, d));
-  CU(cudaSetDevice(c->device));
+  CU(cudaSetDevice(ctx->device));
   const uint32_t nn = d->n_nodes;
   const uint32_t coeffs = (d->sh_degree + 1) * (d->sh_degree + 1);
-  const bool half = c->attr_fp16;
+  const bool half = ctx->attr_fp16;
   const size_t block = cluster_block_bytes(int(coeffs), half);   // bytes per cluster block
   std::vector<float4> own(nn), par(nn), bound(nn);
   std::vector<float> sigma(nn);
@@ -662,10 +855,10 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
     for (DevBuf* b : bs) dfree(c, *b);
     return s;
   }
-  c->assets.push_back(std::move(a));
-  std::vector<AssetDev> table(c->assets.size());
-  for (size_t i = 0; i < c->assets.size(); ++i) {
-    const AssetHost& h = c->assets[i];
+  ctx->assets.push_back(std::move(a));
+  std::vector<AssetDev> table(ctx->assets.size());
+  for (size_t i = 0; i < ctx->assets.size(); ++i) {
+    const AssetHost& h = ctx->assets[i];
     AssetDev& t = table[i];
     t.own = P<float4>(h.own);
     t.par = P<float4>(h.par);
@@ -679,19 +872,20 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* c, const v3dg_hierarchy_desc* d, uint3
     t.sh_coeffs = h.sh_coeffs;
     t.half_color = h.half_color ? 1u : 0u;
   }
-  ST(ensure(c, c->d_assets, sizeof(AssetDev) * table.size()));
-  CU(cudaMemcpy(c->d_assets.p, table.data(), sizeof(AssetDev) * table.size(), cudaMemcpyHostToDevice));
-  if (asset_id) *asset_id = uint32_t(c->assets.size() - 1);
+  ST(ensure(c, ctx->d_assets, sizeof(AssetDev) * table.size()));
+  CU(cudaMemcpy(ctx->d_assets.p, table.data(), sizeof(AssetDev) * table.size(), cudaMemcpyHostToDevice));
+  if (asset_id) *asset_id = uint32_t(ctx->assets.size() - 1);
   c->err.clear();
   return V3DG_OK;
 }
 
-v3dg_status v3dg_set_instances(v3dg_ctx* c, uint32_t n, const uint32_t* asset_id, const double* rot, const double* trans,
+v3dg_status v3dg_set_instances(v3dg_ctx* ctx, uint32_t n, const uint32_t* asset_id, const double* rot, const double* trans,
                                const double* scale) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
   if (n && (!asset_id || !rot || !trans || !scale)) return fail(c, V3DG_EINVAL, "NULL instance array");
   for (uint32_t i = 0; i < n; ++i) {
-    if (asset_id[i] >= c->assets.size()) return fail(c, V3DG_ENOTFOUND, "instance %u: unknown asset %u", i, asset_id[i]);
+    if (asset_id[i] >= ctx->assets.size()) return fail(c, V3DG_ENOTFOUND, "instance %u: unknown asset %u", i, asset_id[i]);
     if (!(scale[i] > 0.0) || !std::isfinite(scale[i])) return fail(c, V3DG_EINVAL, "instance %u: scale must be > 0", i);
     for (int q = 0; q < 9; ++q)
       if (!std::isfinite(rot[9 * size_t(i) + q])) return fail(c, V3DG_EINVAL, "instance %u: rotation not finite", i);
@@ -707,9 +901,10 @@ v3dg_status v3dg_set_instances(v3dg_ctx* c, uint32_t n, const uint32_t* asset_id
   return V3DG_OK;
 }
 
-v3dg_status v3dg_select(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
+v3dg_status v3dg_select(v3dg_ctx* ctx, const v3dg_camera* cam, float tau_px) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
-  CU(cudaSetDevice(c->device));
+  CU(cudaSetDevice(ctx->device));
   ST(setup_frame(c, cam, tau_px));
   ST(enqueue_select(c));
   c->selected = true;
@@ -718,23 +913,25 @@ v3dg_status v3dg_select(v3dg_ctx* c, const v3dg_camera* cam, float tau_px) {
   return V3DG_OK;
 }
 
-v3dg_status v3dg_render(v3dg_ctx* c, float* rgb_out, float* t_out) {
+v3dg_status v3dg_render(v3dg_ctx* ctx, float* rgb_out, float* t_out) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
   if (!c->selected) return fail(c, V3DG_ENOTFOUND, "v3dg_render without a prior v3dg_select");
   if (!rgb_out) return fail(c, V3DG_EINVAL, "rgb_out is NULL");
-  ST(run_frame(c, rgb_out, t_out));
+  ST(run_frame(c, rgb_out, t_out, ctx->sync_check));
   c->err.clear();
   return V3DG_OK;
 }
 
-v3dg_status v3dg_render_host(v3dg_ctx* c, float* rgb_host, float* t_host) {
+v3dg_status v3dg_render_host(v3dg_ctx* ctx, float* rgb_host, float* t_host) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
   if (!c->selected) return fail(c, V3DG_ENOTFOUND, "v3dg_render_host without a prior v3dg_select");
   if (!rgb_host) return fail(c, V3DG_EINVAL, "rgb_host is NULL");
   const size_t px = size_t(c->cam.width) * size_t(c->cam.height);
   ST(ensure(c, c->d_img, sizeof(float) * 3 * px));
   if (t_host) ST(ensure(c, c->d_timg, sizeof(float) * px));
-  ST(run_frame(c, P<float>(c->d_img), t_host ? P<float>(c->d_timg) : nullptr));
+  ST(run_frame(c, P<float>(c->d_img), t_host ? P<float>(c->d_timg) : nullptr, ctx->sync_check));
   CU(cudaMemcpyAsync(rgb_host, c->d_img.p, sizeof(float) * 3 * px, cudaMemcpyDeviceToHost, c->stream));
   if (t_host) CU(cudaMemcpyAsync(t_host, c->d_timg.p, sizeof(float) * px, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -744,7 +941,8 @@ v3dg_status v3dg_render_host(v3dg_ctx* c, float* rgb_host, float* t_host) {
   return V3DG_OK;
 }
 
-v3dg_status v3dg_frame_stats(v3dg_ctx* c, v3dg_stats* out) {
+v3dg_status v3dg_frame_stats(v3dg_ctx* ctx, v3dg_stats* out) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c || !out) return V3DG_EINVAL;
   if (!c->selected) return fail(c, V3DG_ENOTFOUND, "no frame selected");
   ST(sync_frame(c));
@@ -758,7 +956,7 @@ v3dg_status v3dg_frame_stats(v3dg_ctx* c, v3dg_stats* out) {
   CU(cudaMemset(P<uint32_t>(c->d_misc) + 12, 0, sizeof sticky));
   out->overflow = f[kOverflow] | sticky[0];
   out->timeout = f[kTimeout] | sticky[1];
-  if (c->count_work) std::memcpy(&out->blend_evals, c->h_tmp + kFrameWords, 2 * sizeof(unsigned long long));
+  if (ctx->count_work) std::memcpy(&out->blend_evals, c->h_tmp + kFrameWords, 2 * sizeof(unsigned long long));
   uint32_t ncut = 0, ng = 0;
   ST(run_cut(c, &ncut, &ng));
   out->cut_nodes = ncut;
@@ -767,7 +965,8 @@ v3dg_status v3dg_frame_stats(v3dg_ctx* c, v3dg_stats* out) {
   return V3DG_OK;
 }
 
-v3dg_status v3dg_get_cut(v3dg_ctx* c, uint32_t* inst_node, uint64_t cap, uint64_t* n) {
+v3dg_status v3dg_get_cut(v3dg_ctx* ctx, uint32_t* inst_node, uint64_t cap, uint64_t* n) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c || !n) return V3DG_EINVAL;
   uint32_t ncut = 0, ng = 0;
   ST(run_cut(c, &ncut, &ng));
@@ -780,8 +979,9 @@ v3dg_status v3dg_get_cut(v3dg_ctx* c, uint32_t* inst_node, uint64_t cap, uint64_
   return V3DG_OK;
 }
 
-v3dg_status v3dg_get_projected(v3dg_ctx* c, uint64_t cap, uint64_t* n, uint32_t* inst, uint32_t* local, float* u,
+v3dg_status v3dg_get_projected(v3dg_ctx* ctx, uint64_t cap, uint64_t* n, uint32_t* inst, uint32_t* local, float* u,
                                float* conic, float* opacity, float* rgb, uint32_t* depth_key, int32_t* rect) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c || !n) return V3DG_EINVAL;
   if (!c->rendered) return fail(c, V3DG_ENOTFOUND, "no frame rendered");
   ST(sync_frame(c));
@@ -817,7 +1017,7 @@ v3dg_status v3dg_get_projected(v3dg_ctx* c, uint64_t cap, uint64_t* n, uint32_t*
     std::memcpy(&org, &r2.y, 4);
     const uint2 rr = rc[slot];
     if (inst) inst[q] = e.x;
-    if (local) local[q] = c->assets[c->inst_asset[e.x]].node_first[e.y] + j;
+    if (local) local[q] = ctx->assets[c->inst_asset[e.x]].node_first[e.y] + j;
     if (u) {
       u[2 * q] = float(double(r0.x) + 16.0 * double(org & 0xFFFFu));
       u[2 * q + 1] = float(double(r0.y) + 16.0 * double(org >> 16));
@@ -845,8 +1045,9 @@ v3dg_status v3dg_get_projected(v3dg_ctx* c, uint64_t cap, uint64_t* n, uint32_t*
   return V3DG_OK;
 }
 
-v3dg_status v3dg_get_pairs(v3dg_ctx* c, uint64_t cap, uint64_t* n, uint32_t* tile, uint32_t* depth_key, uint32_t* inst,
+v3dg_status v3dg_get_pairs(v3dg_ctx* ctx, uint64_t cap, uint64_t* n, uint32_t* tile, uint32_t* depth_key, uint32_t* inst,
                            uint32_t* local) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c || !n) return V3DG_EINVAL;
   if (!c->rendered) return fail(c, V3DG_ENOTFOUND, "no frame rendered");
   ST(sync_frame(c));
@@ -876,13 +1077,14 @@ v3dg_status v3dg_get_pairs(v3dg_ctx* c, uint64_t cap, uint64_t* n, uint32_t* til
     const uint2 e = list[slot / kSlots];
     if (depth_key) depth_key[q] = key_of[slot];
     if (inst) inst[q] = e.x;
-    if (local) local[q] = c->assets[c->inst_asset[e.x]].node_first[e.y] + slot % kSlots;
+    if (local) local[q] = ctx->assets[c->inst_asset[e.x]].node_first[e.y] + slot % kSlots;
   }
   c->err.clear();
   return V3DG_OK;
 }
 
-v3dg_status v3dg_get_tile_ranges(v3dg_ctx* c, uint32_t* range, uint64_t cap, uint64_t* n_tiles) {
+v3dg_status v3dg_get_tile_ranges(v3dg_ctx* ctx, uint32_t* range, uint64_t cap, uint64_t* n_tiles) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c || !n_tiles) return V3DG_EINVAL;
   if (!c->rendered) return fail(c, V3DG_ENOTFOUND, "no frame rendered");
   ST(sync_frame(c));
@@ -893,11 +1095,12 @@ v3dg_status v3dg_get_tile_ranges(v3dg_ctx* c, uint32_t* range, uint64_t cap, uin
   return V3DG_OK;
 }
 
-v3dg_status v3dg_stage_times(v3dg_ctx* c, float* ms, int n, uint64_t* launches) {
+v3dg_status v3dg_stage_times(v3dg_ctx* ctx, float* ms, int n, uint64_t* launches) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
-  if (launches) *launches = c->launches;
+  if (launches) *launches = ctx->launches;
   if (ms && n > 0) {
-    if (!c->stage_timing || !c->rendered) return fail(c, V3DG_ENOTFOUND, "stage timing is off or no frame rendered");
+    if (!ctx->stage_timing || !c->rendered) return fail(c, V3DG_ENOTFOUND, "stage timing is off or no frame rendered");
     CU(cudaStreamSynchronize(c->stream));
     for (int i = 0; i < n && i < kStages; ++i) CU(cudaEventElapsedTime(ms + i, c->ev[i], c->ev[i + 1]));
   }
@@ -905,13 +1108,14 @@ v3dg_status v3dg_stage_times(v3dg_ctx* c, float* ms, int n, uint64_t* launches) 
   return V3DG_OK;
 }
 
-v3dg_status v3dg_sort_pairs(v3dg_ctx* c, uint32_t* keys, uint32_t* vals, uint64_t n, int begin_bit, int end_bit) {
+v3dg_status v3dg_sort_pairs(v3dg_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t n, int begin_bit, int end_bit) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
   if (n == 0) return V3DG_OK;
   if (!keys || !vals) return fail(c, V3DG_EINVAL, "NULL keys or values");
   if (n > kMaxPairs) return fail(c, V3DG_EINVAL, "n = %llu exceeds %u", (unsigned long long)n, kMaxPairs);
   if (begin_bit < 0 || end_bit > 32 || begin_bit >= end_bit) return fail(c, V3DG_EINVAL, "bad bit range [%d, %d)", begin_bit, end_bit);
-  CU(cudaSetDevice(c->device));
+  CU(cudaSetDevice(ctx->device));
   ST(ensure(c, c->d_sort_k, 4 * n));
   ST(ensure(c, c->d_sort_v, 4 * n));
   ST(ensure_status(c, ((n + kSortTile - 1) / kSortTile) * 256));
@@ -923,9 +1127,9 @@ v3dg_status v3dg_sort_pairs(v3dg_ctx* c, uint32_t* keys, uint32_t* vals, uint64_
   bool in1 = false;
   int nl = 0;
   CU(launch_sort(keys, vals, P<uint32_t>(c->d_sort_k), P<uint32_t>(c->d_sort_v), misc, uint32_t(n), begin_bit, end_bit,
-                 false, sort_scratch(c, misc + 1), misc + 5, c->epoch, c->sm_count, c->stream, &in1, &nl));
+                 false, sort_scratch(c, misc + 1), misc + 5, c->epoch, ctx->sm_count, c->stream, &in1, &nl));
   next_epoch(c);
-  c->launches += nl + 1;
+  ctx->launches += nl + 1;
   if (in1) {
     CU(cudaMemcpyAsync(keys, c->d_sort_k.p, 4 * n, cudaMemcpyDeviceToDevice, c->stream));
     CU(cudaMemcpyAsync(vals, c->d_sort_v.p, 4 * n, cudaMemcpyDeviceToDevice, c->stream));
@@ -934,6 +1138,106 @@ v3dg_status v3dg_sort_pairs(v3dg_ctx* c, uint32_t* keys, uint32_t* vals, uint64_
   CU(cudaStreamSynchronize(c->stream));
   if (c->h_tmp[0]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up; output invalid");
   c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_server_start(v3dg_ctx* ctx, int slots, uint64_t hbm_budget) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
+  if (!c) return V3DG_EINVAL;
+  if (slots < 1 || slots > 64) return fail(c, V3DG_EINVAL, "slots must be in [1, 64]");
+  if (ctx->server) return fail(c, V3DG_EBUSY, "the server is already running");
+  if (ctx->assets.empty()) return fail(c, V3DG_ENOTFOUND, "no hierarchy loaded");
+  CU(cudaSetDevice(ctx->device));
+  Server* sv = new (std::nothrow) Server;
+  if (!sv) return fail(c, V3DG_ENOMEM, "out of host memory");
+  sv->ctx = ctx;
+  sv->budget = hbm_budget ? hbm_budget : ~uint64_t(0);
+  for (int i = 0; i < slots; ++i) {
+    auto p = std::make_unique<Pipe>();
+    p->ctx_alloc = false;   // workers use cudaMalloc: the allocator is called from the owner's thread only
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      ctx->server = sv;
+      server_stop(ctx);
+      return fail(c, V3DG_ECUDA, "cudaStreamCreate failed");
+    }
+    const v3dg_status s = pipe_init(ctx, p.get(), st);
+    sv->slots.push_back(std::move(p));
+    if (s != V3DG_OK) {
+      ctx->server = sv;
+      server_stop(ctx);
+      return fail(c, s, "slot set-up failed");
+    }
+  }
+  ctx->server = sv;
+  for (auto& p : sv->slots) sv->threads.emplace_back(slot_main, sv, p.get());
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_server_stop(v3dg_ctx* ctx) {
+  if (!ctx) return V3DG_EINVAL;
+  server_stop(ctx);
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_submit(v3dg_ctx* ctx, const v3dg_request* req, uint64_t* ticket) {
+  if (!ctx || !req || !ticket) return V3DG_EINVAL;
+  Server* sv = ctx->server;
+  if (!sv) return V3DG_ENOTFOUND;
+  const uint32_t n = req->n_instances;
+  if (n && (!req->asset_id || !req->rot || !req->trans || !req->scale)) return V3DG_EINVAL;
+  if (!req->rgb_out) return V3DG_EINVAL;
+  const v3dg_camera& cam = req->camera;
+  if (cam.width <= 0 || cam.height <= 0 || !(cam.fx > 0.f) || !(cam.fy > 0.f) || !(req->tau_px >= 0.f))
+    return V3DG_EINVAL;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (req->asset_id[i] >= ctx->assets.size()) return V3DG_ENOTFOUND;
+    if (!(req->scale[i] > 0.0) || !std::isfinite(req->scale[i])) return V3DG_EINVAL;
+  }
+  Request rq;
+  rq.asset.assign(req->asset_id, req->asset_id + n);
+  rq.rot.assign(req->rot, req->rot + 9 * size_t(n));
+  rq.trans.assign(req->trans, req->trans + 3 * size_t(n));
+  rq.scale.assign(req->scale, req->scale + n);
+  rq.cam = cam;
+  rq.tau_px = req->tau_px;
+  rq.rgb = req->rgb_out;
+  rq.t = req->t_out;
+  rq.out_device = req->out_on_device != 0;
+  rq.est_bytes = request_bytes(n, cam);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) return V3DG_EBUSY;
+    rq.ticket = sv->next_ticket++;
+    rq.t_submit = sv->now_ms();
+    *ticket = rq.ticket;
+    sv->pending.insert(rq.ticket);
+    sv->queue.push_back(std::move(rq));
+  }
+  sv->cv_work.notify_one();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_poll(v3dg_ctx* ctx, uint64_t ticket, uint32_t timeout_us, v3dg_result* out) {
+  if (!ctx || !out) return V3DG_EINVAL;
+  Server* sv = ctx->server;
+  if (!sv) return V3DG_ENOTFOUND;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  if (!sv->pending.count(ticket)) return V3DG_ENOTFOUND;
+  const bool ready = sv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us),
+                                          [&] { return sv->finished.count(ticket) != 0; });
+  if (!ready) return V3DG_EBUSY;
+  const Finished f = sv->finished[ticket];
+  sv->finished.erase(ticket);
+  sv->pending.erase(ticket);
+  std::memset(out, 0, sizeof *out);
+  out->status = f.status;
+  out->submit_ms = f.t_submit;
+  out->start_ms = f.t_start;
+  out->done_ms = f.t_done;
+  out->visible = f.visible;
+  out->pairs = f.pairs;
   return V3DG_OK;
 }
 

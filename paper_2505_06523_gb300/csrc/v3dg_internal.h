@@ -97,9 +97,12 @@ cudaError_t launch_noderef(const uint2* render_list, uint32_t cap_nodes, const I
 // with (u_rel, v_rel) the 2D mean relative to the pixel origin of the Gaussian's first tile
 // (tx0, ty0), log2(alpha) = na dx^2 + nb dx dy + nc dy^2 + log2 o, and the inclusive pixel
 // ranges x0 | x1 << 16, y0 | y1 << 16 of the alpha >= 1/255 ellipse's bounding box.
+// color_formats: bit 0 set if some loaded asset stores its colour planes in float32, bit 1 if
+// some asset stores them in float16 (the kernel is specialised for the formats present).
 cudaError_t launch_project(const uint2* render_list, uint32_t cap_nodes, const InstFrame* inst,
                            const AssetDev* assets, const CamConst& cam, const float4* ref, float4* rec,
-                           uint2* rect, uint32_t* keys, uint32_t* frame, int sm_count, cudaStream_t st);
+                           uint2* rect, uint32_t* keys, uint32_t* frame, int color_formats, int sm_count,
+                           cudaStream_t st);
 
 // Radix sort of (key, value) pairs, n read from *n_dev (clamped to cap).  Ping-pongs between
 // (k0, v0) and (k1, v1); the result lands in (k0, v0) when the pass count is even, else in
