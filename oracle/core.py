@@ -425,6 +425,75 @@ def render_pixels(p: Projected, pixels) -> tuple[np.ndarray, np.ndarray, np.ndar
     return np.array(out_c).reshape(-1, 3), np.array(out_t), np.array(out_b, bool)
 
 
+def node_mean_balls(asset):
+    """Per node: a ball holding the means of its Gaussians and their largest standard deviation.
+
+    Centre = mean of the node's Gaussian means, radius = the largest distance from it (both
+    FP64, asset frame), sigma = max over the node's Gaussians of exp(max log-scale).  Used only
+    to bound where a node's Gaussians can land on screen.
+    """
+    first = asset.node_first.astype(np.int64)
+    cnt = asset.node_count.astype(np.int64)
+    start = np.cumsum(cnt) - cnt
+    idx = np.repeat(first, cnt) + (np.arange(int(cnt.sum())) - np.repeat(start, cnt))
+    mu = asset.means[idx].astype(np.float64)
+    centre = np.add.reduceat(mu, start, axis=0) / cnt[:, None]
+    d = np.sqrt(((mu - np.repeat(centre, cnt, axis=0)) ** 2).sum(axis=1))
+    radius = np.maximum.reduceat(d, start)
+    sigma = np.exp(np.maximum.reduceat(asset.log_scales[idx].astype(np.float64).max(axis=1), start))
+    return centre, radius, sigma
+
+
+def nodes_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float = 1.0) -> Cut:
+    """The nodes of the cut whose Gaussians can have alpha >= 1/255 at one of the pixels.
+
+    A conservative screen bound per (instance, node), so that the per-pixel definition at a
+    few pixels of a large frame needs only these nodes' Gaussians projected.  With the node's
+    means in the view-space ball (c, R) (R = s r) and c_z - R = z_min > near:
+      * a mean p of the ball has |p_x / p_z - c_x / c_z| <= R sqrt(c_x^2 + c_z^2) / (c_z z_min)
+        (and likewise in y), so its pixel mean is within f_x times that of f_x c_x / c_z + c_x0;
+      * the EWA Jacobian at the clamped mean has ||J||_2 <= sqrt(f_x^2 (1 + l_x^2) + f_y^2
+        (1 + l_y^2)) / z_min (Frobenius bound, |x'/z| <= l_x, |y'/z| <= l_y), and the view-space
+        covariance has largest eigenvalue (s sigma)^2, so the alpha >= 1/255 ellipse
+        (q <= 2 ln(255 o) <= 2 ln 255) lies within sqrt(2 ln 255) ||J||_2 s sigma of the mean.
+    Nodes with z_min <= near are always kept.  The bound is widened by 2 px (the margin of
+    render_pixels) plus ``slack_px``.
+    """
+    m_all = compose(cam.world_to_cam, inst.rot, inst.trans, inst.scale)
+    fx, fy, cx, cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    limx = CLAMP_FOV * (0.5 * cam.width / fx)
+    limy = CLAMP_FOV * (0.5 * cam.height / fy)
+    jn = math.sqrt(fx * fx * (1.0 + limx * limx) + fy * fy * (1.0 + limy * limy))
+    ksig = math.sqrt(2.0 * math.log(255.0))
+    q = np.asarray([(px + 0.5, py + 0.5) for px, py in pixels], np.float64).reshape(-1, 2)
+    balls = {}
+    keep = np.zeros(len(cut.inst), bool)
+    for i in np.unique(cut.inst):
+        sel = np.nonzero(cut.inst == i)[0]
+        a_id = int(inst.asset[i])
+        if a_id not in balls:
+            balls[a_id] = node_mean_balls(assets[a_id])
+        centre, radius, sigma = balls[a_id]
+        nodes = cut.node[sel].astype(np.int64)
+        m = m_all[i]
+        s = float(inst.scale[i])
+        cv = centre[nodes] @ m[:, :3].T + m[:, 3]
+        rv = s * radius[nodes]
+        zmin = cv[:, 2] - rv
+        front = zmin > float(cam.near)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ux = fx * cv[:, 0] / cv[:, 2] + cx
+            uy = fy * cv[:, 1] / cv[:, 2] + cy
+            spread = ksig * jn * s * sigma[nodes] / zmin + 2.0 + slack_px
+            dx = fx * rv * np.sqrt(cv[:, 0] ** 2 + cv[:, 2] ** 2) / (cv[:, 2] * zmin) + spread
+            dy = fy * rv * np.sqrt(cv[:, 1] ** 2 + cv[:, 2] ** 2) / (cv[:, 2] * zmin) + spread
+        hit = ~front
+        for qx, qy in q:
+            hit |= front & (np.abs(qx - ux) <= dx) & (np.abs(qy - uy) <= dy)
+        keep[sel] = hit
+    return Cut(cut.inst[keep], cut.node[keep], cut.ties)
+
+
 def render_image(p: Projected, width: int, height: int):
     """Whole image by the per-pixel definition, processed Gaussian by Gaussian.
 

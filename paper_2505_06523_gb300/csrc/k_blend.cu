@@ -1,8 +1,9 @@
 // Per-tile front-to-back alpha blending (Sec. 2.1): C = sum_i c_i a_i prod_{j<i} (1 - a_j).
 //
 // One 256-thread block per 16x16 tile, or per 8x8 quadrant of a tile with a long list
-// (persistent blocks take work items heaviest-first: tiles differ in cost by orders of magnitude).  The tile's depth-ordered records are taken in batches of up to
-// 256; each batch runs in two phases:
+// (persistent blocks take work items heaviest-first: tiles differ in cost by orders of magnitude).
+// The tile's depth-ordered records are taken in batches of up to 256; each batch runs in two
+// phases:
 //  - record-parallel test: the batch's (record, pixel) pairs -- every pixel of the record's
 //    alpha >= 1/255 pixel box that is still accumulating -- are spread evenly over the threads;
 //    a pair whose alpha passes the skip rule sets the record's bit in that pixel's 256-bit mask;
@@ -23,6 +24,9 @@ namespace {
 
 constexpr int kBlendThreads = 256;
 constexpr int kBlendWarps = kBlendThreads / 32;
+constexpr int kBatch = 256;                    // records staged per batch
+constexpr int kPer = kBatch / kBlendThreads;   // consecutive records staged per thread
+constexpr int kMaskWords = kBatch / 32;        // per-pixel mask words
 constexpr float kLog2MinAlpha = -7.9943534f;  // log2(1/255)
 
 // log2(alpha) of a staged record at tile-local pixel centre (fx, fy); one definition for both phases
@@ -57,14 +61,14 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
     if (frame[kOverflow]) atomicOr(sticky, 1u);
     if (frame[kTimeout]) atomicOr(sticky + 1, 1u);
   }
-  __shared__ float4 s_g[kBlendThreads];             // (u, v, na, nb) in this tile's pixel frame
-  __shared__ float4 s_c[kBlendThreads];             // (nc, log2 o, r, g)
-  __shared__ float s_b[kBlendThreads];              // b
-  __shared__ uint32_t s_box[kBlendThreads];         // clipped box: x0 | x1 << 8 | y0 << 16 | y1 << 24
-  __shared__ uint32_t s_eoff[kBlendThreads + 1];    // exclusive prefix of the box areas
-  __shared__ uint32_t s_mask[kBlendThreads][kBlendWarps];  // [pixel][record word]: contributing records
+  __shared__ float4 s_g[kBatch];                    // (u, v, na, nb) in this tile's pixel frame
+  __shared__ float4 s_c[kBatch];                    // (nc, log2 o, r, g)
+  __shared__ float s_b[kBatch];                     // b
+  __shared__ uint32_t s_box[kBatch];                // clipped box: x0 | x1 << 8 | y0 << 16 | y1 << 24
+  __shared__ uint32_t s_eoff[kBatch + 1];           // exclusive prefix of the box areas
+  __shared__ uint32_t s_mask[kBlendThreads][kMaskWords];  // [pixel][record word]: contributing records
   __shared__ uint32_t s_done[kBlendWarps];          // finished pixels, one word per row pair
-  __shared__ uint32_t s_qslot[kBlendThreads];       // the batch: slots of the records to stage, in order
+  __shared__ uint32_t s_qslot[kBatch];              // a filtered batch: slots of the records, in order
   __shared__ uint32_t s_scan[kBlendWarps + 1];
   __shared__ uint32_t s_next, s_resume;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -72,7 +76,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
   const float fx = float(lx) + 0.5f, fy = float(ly) + 0.5f;
   uint32_t n_eval = 0, n_contrib = 0;
 #pragma unroll
-  for (int k = 0; k < kBlendWarps; ++k) s_mask[threadIdx.x][k] = 0u;
+  for (int k = 0; k < kMaskWords; ++k) s_mask[threadIdx.x][k] = 0u;
   for (;;) {
     if (threadIdx.x == 0) s_next = atomicAdd(tile_counter, 1u);
     __syncthreads();
@@ -101,14 +105,14 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
 #pragma unroll
       for (int w = 0; w < kBlendWarps; ++w) act |= uint32_t(s_done[w] != 0xffffffffu) << w;
       if (act == 0 || sp >= range.y) break;
-      // fill the batch with the next records whose box reaches a live row pair, in list order
+      // the batch: the next kBatch records of the list when every row pair is live, else the next
+      // records whose box reaches a live row pair of the item, in list order
       uint32_t q = 0;
-      if (region == 0 && act == (1u << kBlendWarps) - 1u) {   // every row pair live: every record is relevant
-        q = min(uint32_t(kBlendThreads), range.y - sp);
-        if (threadIdx.x < q) s_qslot[threadIdx.x] = pv[sp + threadIdx.x];
-        sp += q;
+      const bool all_live = region == 0 && act == (1u << kBlendWarps) - 1u;
+      if (all_live) {
+        q = min(uint32_t(kBatch), range.y - sp);
       } else {
-        while (q < uint32_t(kBlendThreads) && sp < range.y) {
+        while (q < uint32_t(kBatch) && sp < range.y) {
           constexpr int kScan = 4;   // records tested per thread and step
           const uint32_t i0 = sp + threadIdx.x * kScan;
           uint32_t sl[kScan], hits = 0;
@@ -130,81 +134,108 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
 #pragma unroll
           for (int k = 0; k < kScan; ++k) {
             if ((hits >> k) & 1u) {
-              if (pos < uint32_t(kBlendThreads)) s_qslot[pos] = sl[k];
-              else if (pos == uint32_t(kBlendThreads)) s_resume = i0 + k;   // first record left over
+              if (pos < uint32_t(kBatch)) s_qslot[pos] = sl[k];
+              else if (pos == uint32_t(kBatch)) s_resume = i0 + k;   // first record left over
               ++pos;
             }
           }
           __syncthreads();
-          if (q + total > uint32_t(kBlendThreads)) {
+          if (q + total > uint32_t(kBatch)) {
             sp = s_resume;
-            q = kBlendThreads;
+            q = kBatch;
           } else {
             sp = min(sp + uint32_t(kBlendThreads * kScan), range.y);
             q += total;
           }
         }
+        __syncthreads();
+        if (q == 0) break;
       }
-      __syncthreads();
-      if (q == 0) break;
-      // stage the batch; each record's (clipped) box area in this tile
-      uint32_t area = 0;
-      if (threadIdx.x < q) {
-        const uint32_t slot = s_qslot[threadIdx.x];
-        if (slot < cap_slots) {
-          const float4* r = rec + 3 * size_t(slot);
-          const float4 r0 = r[0], r1 = r[1], r2 = r[2];
-          const uint32_t org = __float_as_uint(r2.y);
-          const float ox = float(16 * (tx - int(org & 0xFFFFu))), oy = float(16 * (ty - int(org >> 16)));
-          s_g[threadIdx.x] = make_float4(r0.x - ox, r0.y - oy, r0.z, r0.w);
-          s_c[threadIdx.x] = r1;
-          s_b[threadIdx.x] = r2.x;
-          int x0, x1, y0, y1;
-          box_in_tile(r2, tx, ty, &x0, &x1, &y0, &y1);
-          x0 = max(x0, qx0); x1 = min(x1, qx1); y0 = max(y0, qy0); y1 = min(y1, qy1);
-          if (x0 <= x1 && y0 <= y1) {
-            area = uint32_t((x1 - x0 + 1) * (y1 - y0 + 1));
-            s_box[threadIdx.x] = uint32_t(x0) | (uint32_t(x1) << 8) | (uint32_t(y0) << 16) | (uint32_t(y1) << 24);
+      // stage the batch (kPer consecutive records per thread); each record's clipped box area
+      uint32_t area[kPer], asum = 0;
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const uint32_t i = threadIdx.x * kPer + k;
+        area[k] = 0;
+        if (i < q) {
+          const uint32_t slot = all_live ? pv[sp + i] : s_qslot[i];
+          if (slot < cap_slots) {
+            const float4* r = rec + 3 * size_t(slot);
+            const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+            const uint32_t org = __float_as_uint(r2.y);
+            const float ox = float(16 * (tx - int(org & 0xFFFFu))), oy = float(16 * (ty - int(org >> 16)));
+            s_g[i] = make_float4(r0.x - ox, r0.y - oy, r0.z, r0.w);
+            s_c[i] = r1;
+            s_b[i] = r2.x;
+            int x0, x1, y0, y1;
+            box_in_tile(r2, tx, ty, &x0, &x1, &y0, &y1);
+            x0 = max(x0, qx0); x1 = min(x1, qx1); y0 = max(y0, qy0); y1 = min(y1, qy1);
+            if (x0 <= x1 && y0 <= y1) {
+              area[k] = uint32_t((x1 - x0 + 1) * (y1 - y0 + 1));
+              s_box[i] = uint32_t(x0) | (uint32_t(x1) << 8) | (uint32_t(y0) << 16) | (uint32_t(y1) << 24);
+            }
           }
         }
+        asum += area[k];
       }
+      if (all_live) sp += q;
       uint32_t n_pairs;
-      const uint32_t eoff = block_exclusive_scan<kBlendWarps>(area, s_scan, &n_pairs);
-      s_eoff[threadIdx.x] = eoff;   // records q..255 have area 0, so s_eoff[q] = n_pairs
-      if (threadIdx.x == 0) s_eoff[kBlendThreads] = n_pairs;
+      uint32_t eoff = block_exclusive_scan<kBlendWarps>(asum, s_scan, &n_pairs);
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {   // records q.. have area 0, so s_eoff[q] = n_pairs
+        s_eoff[threadIdx.x * kPer + k] = eoff;
+        eoff += area[k];
+      }
+      if (threadIdx.x == 0) s_eoff[kBatch] = n_pairs;
       __syncthreads();
       // record-parallel alpha test of the batch's (record, pixel) pairs, spread evenly
       {
         // this thread's contiguous share of the pairs; its first record by binary search
         const uint32_t per = (n_pairs + kBlendThreads - 1) / kBlendThreads;
         const uint32_t e0 = min(threadIdx.x * per, n_pairs), e1 = min(e0 + per, n_pairs);
-        uint32_t j = 0;
         if (e0 < e1) {
           uint32_t lo = 0, hi = q;   // last record with s_eoff[lo] <= e0 (s_eoff[q] = n_pairs > e0)
           while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
             if (s_eoff[mid] <= e0) lo = mid; else hi = mid;
           }
-          j = lo;
-        }
-        for (uint32_t e = e0; e < e1; ++e) {
-          while (s_eoff[j + 1] <= e) ++j;   // e only grows, so the record index only moves forward
-          const uint32_t b = s_box[j];
-          const int x0 = int(b & 0xFFu), x1 = int((b >> 8) & 0xFFu), y0 = int((b >> 16) & 0xFFu);
-          const int w = x1 - x0 + 1;
-          const int k = int(e - s_eoff[j]);
-          const int yy = y0 + k / w, xx = x0 + k % w;
-          if ((s_done[yy >> 1] >> ((yy & 1) * 16 + xx)) & 1u) continue;   // pixel already finished
-          const float l2a = log2_alpha(s_g[j], s_c[j], float(xx) + 0.5f, float(yy) + 0.5f);
-          if (kCount) ++n_eval;
-          if (l2a >= kLog2MinAlpha && fminf(0.999f, exp2f(l2a)) >= 1.f / 255.f)
-            atomicOr(&s_mask[yy * 16 + xx][j >> 5], 1u << (j & 31));
+          uint32_t j = lo;
+          uint32_t e = e0;
+          while (e < e1) {
+            // one record's run of pixels: (xx, yy) advance along the box rows
+            const uint32_t eb = s_eoff[j], ee = s_eoff[j + 1];
+            if (ee == eb) {   // no pixel of this record in the item (its box was not written)
+              ++j;
+              continue;
+            }
+            const uint32_t b = s_box[j];
+            const int x0 = int(b & 0xFFu), x1 = int((b >> 8) & 0xFFu), y0 = int((b >> 16) & 0xFFu);
+            const int w = x1 - x0 + 1;
+            const int k = int(e - eb);
+            int yy = y0 + k / w, xx = x0 + k % w;
+            const uint32_t stop = min(e1, ee);
+            const float4 g = s_g[j], c = s_c[j];
+            const uint32_t bit = 1u << (j & 31);
+            for (; e < stop; ++e) {
+              if (!((s_done[yy >> 1] >> ((yy & 1) * 16 + xx)) & 1u)) {   // pixel still accumulating
+                const float l2a = log2_alpha(g, c, float(xx) + 0.5f, float(yy) + 0.5f);
+                if (kCount) ++n_eval;
+                if (l2a >= kLog2MinAlpha && fminf(0.999f, exp2f(l2a)) >= 1.f / 255.f)
+                  atomicOr(&s_mask[yy * 16 + xx][j >> 5], bit);
+              }
+              if (++xx > x1) {
+                xx = x0;
+                ++yy;
+              }
+            }
+            ++j;
+          }
         }
       }
       __syncthreads();
       // pixel-parallel blend of the contributing records, in depth order
 #pragma unroll
-      for (int wd = 0; wd < kBlendWarps; ++wd) {
+      for (int wd = 0; wd < kMaskWords; ++wd) {
         uint32_t bits = s_mask[threadIdx.x][wd];
         if (!bits) continue;
         s_mask[threadIdx.x][wd] = 0u;
@@ -300,6 +331,12 @@ cudaError_t launch_blend(const uint2* ranges, uint32_t* items, uint32_t* tile_co
   const int n_tiles = cam.tiles_x * cam.tiles_y;
   if (n_tiles == 0) return cudaSuccess;
   uint32_t* n_items = items + 4 * size_t(n_tiles);
+  static const bool carveout_set = [] {   // 4 blocks of 41 KB per SM want the largest carveout
+    cudaFuncSetAttribute(k_blend<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_blend<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return true;
+  }();
+  (void)carveout_set;
   k_blend_items<<<1, 1024, 0, st>>>(ranges, n_tiles, split_pairs, items, n_items);
   const int grid = std::min(4 * n_tiles, sm_count * 4);   // 4 resident blocks per SM (56 registers)
   if (work)

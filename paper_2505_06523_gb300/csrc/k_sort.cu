@@ -16,6 +16,12 @@ constexpr int kWarps = kSortThreads / 32;
 static_assert(kSortThreads >= kBins, "one thread per digit");
 
 // Digit counts of every pass in one read of the keys (one shared histogram per pass and block).
+// A thread counts a run of kHistRun consecutive keys and adds each pass's digit to the shared
+// histogram only when it changes (runs of equal digits are common: the high digits of nearby
+// keys -- depths of one cluster, tiles of one Gaussian -- coincide), which keeps shared-memory
+// atomics on the few hot bins of the high digits from serialising.
+constexpr int kHistRun = 16;
+
 __global__ void __launch_bounds__(256)
 k_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev, uint32_t cap, int begin_bit,
        int end_bit, int passes, uint32_t* __restrict__ hist) {
@@ -23,14 +29,62 @@ k_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev, ui
   for (int i = threadIdx.x; i < 4 * kBins; i += blockDim.x) sh[i / kBins][i % kBins] = 0;
   __syncthreads();
   const uint32_t n = min(*n_dev, cap);
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint32_t k = keys[i];
-    for (int p = 0; p < passes; ++p) {
-      const int sh_ = begin_bit + 8 * p;
-      const uint32_t m = end_bit - sh_ >= 8 ? 0xFFu : ((1u << (end_bit - sh_)) - 1u);
-      atomicAdd(&sh[p][(k >> sh_) & m], 1u);
+  int sh_[4];
+  uint32_t m[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    sh_[p] = begin_bit + 8 * p;
+    m[p] = end_bit - sh_[p] >= 8 ? 0xFFu : ((1u << max(end_bit - sh_[p], 0)) - 1u);
+  }
+  const uint32_t runs = (n + kHistRun - 1) / kHistRun;
+  const bool aligned = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < runs; r += gridDim.x * blockDim.x) {
+    const uint32_t i0 = r * kHistRun;
+    uint32_t cur[4], cnt[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      cur[p] = 0xFFFFFFFFu;
+      cnt[p] = 0;
     }
+    if (aligned && i0 + kHistRun <= n) {   // a full run: four 16-byte loads
+      const uint4* v = reinterpret_cast<const uint4*>(keys + i0);
+#pragma unroll
+      for (int q = 0; q < kHistRun / 4; ++q) {
+        const uint4 k4 = v[q];
+        const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            if (p >= passes) break;
+            const uint32_t d = (kk[t] >> sh_[p]) & m[p];
+            if (d != cur[p]) {
+              if (cnt[p]) atomicAdd(&sh[p][cur[p]], cnt[p]);
+              cur[p] = d;
+              cnt[p] = 0;
+            }
+            ++cnt[p];
+          }
+      }
+    } else {
+      for (uint32_t i = i0; i < min(i0 + kHistRun, n); ++i) {
+        const uint32_t k = keys[i];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          if (p >= passes) break;
+          const uint32_t d = (k >> sh_[p]) & m[p];
+          if (d != cur[p]) {
+            if (cnt[p]) atomicAdd(&sh[p][cur[p]], cnt[p]);
+            cur[p] = d;
+            cnt[p] = 0;
+          }
+          ++cnt[p];
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+      if (cnt[p]) atomicAdd(&sh[p][cur[p]], cnt[p]);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * kBins; i += blockDim.x) {
@@ -168,12 +222,12 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
   k_hist<<<sm_count * 4, 256, 0, st>>>(k0, n_dev, cap, begin_bit, end_bit, passes, sc.hist);
   k_hist_scan<<<1, kBins, 0, st>>>(sc.hist, passes, sc.hist + 4 * kBins);
   *launches += 2;
-  static bool carveout_set = false;
-  if (!carveout_set) {
+  static const bool carveout_set = [] {   // once per process (thread-safe static initialisation)
     cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    carveout_set = true;
-  }
+    return true;
+  }();
+  (void)carveout_set;
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int p = 0; p < passes; ++p) {
     const int shift = begin_bit + 8 * p;

@@ -36,6 +36,14 @@ struct AssetDev {
   uint32_t stride;         // bytes per cluster block: cluster_block_bytes(sh_coeffs, half_color)
   uint32_t sh_coeffs;      // (degree + 1)^2
   uint32_t half_color;     // 1: opacity and SH stored as float16
+  // top-down selection: children of node n are child_list[child_off[n] .. child_off[n + 1]);
+  // sub_bound / sub_sigma bound the spheres and sigmas of every node of n's subtree
+  const uint32_t* child_off;
+  const uint32_t* child_list;
+  const float4* sub_bound;
+  const float* sub_sigma;
+  uint32_t root;
+  uint32_t pad;
 };
 
 // Per (frame, instance) constants, computed on the host in FP64 (128-byte aligned, 256 B).
@@ -68,6 +76,7 @@ enum Counter : int {
   kCutNodes = 0, kCutGauss, kRenderNodes, kVisible, kPairs, kOverflow, kTimeout,
   kSlotCount = 7,          // render nodes (clamped) * 64: the slots the depth sort covers
   kPairsEff = 8,           // pairs the tile sort / blend use: kPairs, or 0 when the frame overflowed
+  kTdReached = 9,          // top-down selection: (instance, node) entries it tested
   kNumCounters = 16,
   kTileCounters = 16,      // [16, 48): atomic tile counters of the chained-scan kernels
   kFrameWords = 48,
@@ -83,6 +92,26 @@ constexpr uint32_t kSpinLimit = 1u << 20;
 cudaError_t launch_select(const InstFrame* inst, int n_inst, const AssetDev* assets, int node_blocks,
                           const CamConst& cam, int mode, uint2* out, uint32_t cap, uint32_t* frame,
                           uint32_t tile_counter_slot, uint64_t* status, uint32_t epoch, cudaStream_t st);
+
+// Top-down selection (same result as launch_select on trees whose footprints never grow from a
+// node to its parent, which the containment of the cluster-group spheres guarantees): level by
+// level from each instance's root, a node whose own footprint exceeds tau_F hands its children
+// to the next level; the others are selected.  mode 0 also skips every subtree whose bound
+// proves the visibility cull of all its nodes.  Marks go to a bitmap of n_inst * wpi words
+// (zeroed by the caller), which one ordered compaction turns into the list of launch_select.
+// frontier: two buffers of cap_front entries; counts: steps + 1 words (zeroed by the caller).
+struct TopDown {
+  uint2* frontier[2];
+  uint32_t cap_front;
+  uint32_t* counts;
+  uint32_t* bitmap;
+  uint32_t wpi;            // bitmap words per instance: ceil(max nodes / 32)
+  int steps;               // largest root level + 1
+};
+cudaError_t launch_select_topdown(const InstFrame* inst, int n_inst, const AssetDev* assets, const CamConst& cam,
+                                  int mode, const TopDown& td, uint2* out, uint32_t cap, uint32_t* frame,
+                                  uint32_t tile_counter_slot, uint64_t* status, uint32_t epoch, int sm_count,
+                                  cudaStream_t st, int* launches);
 
 // Per render-list node, FP64 reference for the projection (2 float4 per node):
 //   [0] = (U0 hi, U0 lo, V0 hi, V0 lo): pixel position of the node's mean centre as float pairs
@@ -114,7 +143,7 @@ struct SortScratch {
   uint32_t max_tiles;
   uint32_t* tile_counters; // one per pass (zeroed by the caller's frame memset)
 };
-constexpr int kSortThreads = 512, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
+constexpr int kSortThreads = 256, kSortItems = 16, kSortTile = kSortThreads * kSortItems;
 cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
                         uint32_t cap, int begin_bit, int end_bit, bool implicit_vals,
                         const SortScratch& sc, uint32_t* err_flag, uint32_t& epoch, int sm_count,
