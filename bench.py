@@ -218,6 +218,14 @@ def main():
     ctx = Context(local)
     for a in assets:
         ctx.load_hierarchy(a)
+    inst16 = None
+    if args.slots > 0:   # the served path's copies of the assets: opacity and SH stored as FP16
+        ctx.set_option(N.V3DG_OPT_ATTR_FP16, 1)
+        for a in assets:
+            ctx.load_hierarchy(a)
+        ctx.set_option(N.V3DG_OPT_ATTR_FP16, 0)
+        inst16 = scenes.subset(inst, np.arange(inst.n))
+        inst16.asset = inst16.asset + np.uint32(len(assets))
     ctx.set_instances(inst)
     cams = [scenes.crowd_camera(t) for t in range(300)]
     frame_ids = replica_frames(rank, world, args.warmup + args.steps)
@@ -267,6 +275,14 @@ def main():
         ctx.render(rgb)
         ms, _ = ctx.stage_times(len(STAGES))
         stage_runs.append(ms)
+    # the same frames with the top-down selection (same cut and image; the select stage differs)
+    ctx.set_option(N.V3DG_OPT_SELECT_TOPDOWN, 1)
+    td_select = []
+    for fid in timed_ids:
+        ctx.select(cams[fid], args.tau)
+        ctx.render(rgb)
+        td_select.append(ctx.stage_times(len(STAGES))[0][0])
+    ctx.set_option(N.V3DG_OPT_SELECT_TOPDOWN, 0)
     ctx.set_option(N.V3DG_OPT_STAGE_TIMING, 0)
     stage_ms = {k: float(np.mean([r[i] for r in stage_runs])) for i, k in enumerate(STAGES)}
     # the blend's algorithmic work on the same frames (a separate, counting replay)
@@ -302,7 +318,16 @@ def main():
 
     served = None
     if args.slots > 0:
-        served = serve_leg(ctx, inst, cams, timed_ids, args.tau, args.slots, args.serve_requests, value)
+        # the autotuner times the blend of one FP16 walk frame with every batch size and split
+        ctx.set_instances(inst16)
+        ctx.select(cams[timed_ids[0]], args.tau)
+        ctx.render(rgb)
+        tuned = ctx.autotune_blend()
+        ctx.set_instances(inst)
+        served = serve_leg(ctx, inst, inst16, cams, timed_ids, args.tau, args.slots, args.serve_requests,
+                           {"batch": tuned["batch"], "split_pairs": tuned["split_pairs"]})
+        served["autotune"] = tuned
+        served["psnr_fp16_vs_fp32_db"] = fp16_psnr(ctx, inst, inst16, cams, timed_ids, args.tau)
 
     peaks, peak_kind = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
@@ -329,6 +354,7 @@ def main():
             "served": served,
             "gpu_launches": int(launches),
             "stages_ms": stage_ms,
+            "select_topdown_ms": float(np.mean(td_select)),
             "frame_mean": {k: int(round(v)) for k, v in fs.items()},
             "stages_sum_ms": float(sum(stage_ms.values())),
             "roofline": roofline,
@@ -348,20 +374,10 @@ def _wait(ctx, ticket):
     return r[0]
 
 
-def serve_leg(ctx, inst, cams, frame_ids, tau, slots, n_req, plain_fps):
-    """The same walk frames as requests to the library's server (v3dg_submit / v3dg_poll), with
-    host buffers like the e2e leg: instances in, image back into pinned host memory.
-
-    closed: `slots` requests always in flight; frames/s over the whole run and per-request latency
-    (submit -> done).  poisson: open-loop Poisson arrivals at 50% and 90% of the closed-loop rate;
-    latency percentiles and the rate achieved."""
-    ctx.server_start(slots)
-    cam_of = lambda k: cams[frame_ids[k % len(frame_ids)]]
-    for t in [ctx.submit(inst, cam_of(k), tau) for k in range(2 * slots)]:   # slots grow their buffers
-        _wait(ctx, t)
-    # closed loop
+def _closed_loop(ctx, inst, cam_of, tau, inflight_n, n_req):
+    """`inflight_n` requests always in flight: frames/s over the run, per-request latencies."""
     lat, t0 = [], time.perf_counter()
-    inflight = [ctx.submit(inst, cam_of(k), tau) for k in range(min(slots, n_req))]
+    inflight = [ctx.submit(inst, cam_of(k), tau) for k in range(min(inflight_n, n_req))]
     nxt = len(inflight)
     while inflight:
         rec = _wait(ctx, inflight.pop(0))
@@ -369,39 +385,106 @@ def serve_leg(ctx, inst, cams, frame_ids, tau, slots, n_req, plain_fps):
         if nxt < n_req:
             inflight.append(ctx.submit(inst, cam_of(nxt), tau))
             nxt += 1
-    closed_s = time.perf_counter() - t0
-    closed_fps = n_req / closed_s
-    out = {"slots": slots, "requests": n_req, "frames": "the timed walk frames, 1000 instances, 1080p, host buffers",
-           "closed": {"value": closed_fps, "unit": "frames/s", "p50_ms": float(np.percentile(lat, 50)),
-                      "p99_ms": float(np.percentile(lat, 99)), "vs_plain_device": closed_fps / plain_fps},
-           "poisson": []}
+    return n_req / (time.perf_counter() - t0), lat
+
+
+def _open_loop(ctx, inst, cam_of, tau, arrivals):
+    """Requests submitted at the given arrival times (s): latencies (submit -> done) and the rate
+    achieved over the run."""
+    pending, lat = [], []
+    t0 = time.perf_counter()
+    k, n_req = 0, len(arrivals)
+    while k < n_req or pending:
+        now = time.perf_counter() - t0
+        while k < n_req and arrivals[k] <= now:
+            pending.append(ctx.submit(inst, cam_of(k), tau))
+            k += 1
+        still = []
+        for t in pending:
+            r = ctx.poll(t, 0)
+            if r is None:
+                still.append(t)
+            else:
+                lat.append(r[0]["done_ms"] - r[0]["submit_ms"])
+        pending = still
+        if pending or k < n_req:
+            time.sleep(0.0005)
+    return n_req / (time.perf_counter() - t0), lat
+
+
+def _pcts(lat):
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+
+DEFAULT_BLEND = {"batch": 256, "split_pairs": 16384}
+
+
+def _blend_options(ctx, opts):
+    from paper_2505_06523_gb300 import _native as N
+    ctx.set_option(N.V3DG_OPT_BLEND_BATCH, opts["batch"])
+    ctx.set_option(N.V3DG_OPT_SPLIT_PAIRS, opts["split_pairs"])
+
+
+def serve_leg(ctx, inst, inst16, cams, frame_ids, tau, slots, n_req, tuned):
+    """Served vs plain on the same request streams, through the library's server (v3dg_submit /
+    v3dg_poll) with host buffers (instances in, image back into pinned host memory).
+
+    plain:  one slot, FP32 attributes, default blend options -- serial one-request-at-a-time
+            rendering;
+    served: `slots` slots whose frames overlap on the GPU, opacity and SH stored as FP16, blend
+            batch and split threshold from the autotuner (`tuned`).
+    closed: as many requests in flight as slots (frames/s = capacity); poisson: open-loop Poisson
+    arrivals at 50% and 90% of the plain capacity, the same arrival times and frames for both."""
+    cam_of = lambda k: cams[frame_ids[k % len(frame_ids)]]
+    arms = {"plain": (1, inst, "FP32 attributes, 1 slot", DEFAULT_BLEND),
+            "served": (slots, inst16, f"FP16 colour, {slots} slots, autotuned blend", tuned)}
+    out = {"requests": n_req, "frames": "the timed walk frames, 1000 instances, 1080p, host buffers"}
+    cap = {}
+    for name, (k, ins, desc, bopts) in arms.items():
+        _blend_options(ctx, bopts)
+        ctx.server_start(k)
+        for t in [ctx.submit(ins, cam_of(j), tau) for j in range(2 * k)]:   # slots grow their buffers
+            _wait(ctx, t)
+        fps, lat = _closed_loop(ctx, ins, cam_of, tau, k, n_req)
+        ctx.server_stop()
+        cap[name] = fps
+        out[name] = {"path": desc, "closed": {"value": fps, "unit": "frames/s", **_pcts(lat)}, "poisson": []}
     rng = np.random.default_rng(7)
     for load in (0.5, 0.9):
-        rate = load * closed_fps
+        rate = load * cap["plain"]
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
-        pending, lat = [], []
-        t0 = time.perf_counter()
-        k = 0
-        while k < n_req or pending:
-            now = time.perf_counter() - t0
-            while k < n_req and arrivals[k] <= now:
-                pending.append(ctx.submit(inst, cam_of(k), tau))
-                k += 1
-            still = []
-            for t in pending:
-                r = ctx.poll(t, 0)
-                if r is None:
-                    still.append(t)
-                else:
-                    lat.append(r[0]["done_ms"] - r[0]["submit_ms"])
-            pending = still
-            if pending or k < n_req:
-                time.sleep(0.0005)
-        span = time.perf_counter() - t0
-        out["poisson"].append({"rate": rate, "achieved": n_req / span, "p50_ms": float(np.percentile(lat, 50)),
-                               "p99_ms": float(np.percentile(lat, 99))})
-    ctx.server_stop()
+        for name, (k, ins, _, bopts) in arms.items():
+            _blend_options(ctx, bopts)
+            ctx.server_start(k)
+            for t in [ctx.submit(ins, cam_of(j), tau) for j in range(k)]:
+                _wait(ctx, t)
+            achieved, lat = _open_loop(ctx, ins, cam_of, tau, arrivals)
+            ctx.server_stop()
+            out[name]["poisson"].append({"rate": rate, "achieved": achieved, **_pcts(lat)})
+    _blend_options(ctx, DEFAULT_BLEND)
+    out["served_vs_plain"] = {
+        "frames_per_s": cap["served"] / cap["plain"],
+        "p99_at_90pct_load": out["served"]["poisson"][1]["p99_ms"] / out["plain"]["poisson"][1]["p99_ms"]}
     return out
+
+
+def fp16_psnr(ctx, inst, inst16, cams, frame_ids, tau):
+    """PSNR (peak 1) of the FP16-colour image against the FP32 one, per walk frame (device images;
+    the FP32 path itself is within 1e-4 of the FP64 oracle in the tests)."""
+    import torch
+    vals = []
+    for f in sorted(set(frame_ids))[:4]:
+        img = []
+        for ins in (inst, inst16):
+            ctx.set_instances(ins)
+            ctx.select(cams[f], tau)
+            img.append(ctx.render()[0].double())
+        mse = float(((img[0] - img[1]) ** 2).mean())
+        vals.append(float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse))
+        del img
+    ctx.set_instances(inst)
+    torch.cuda.synchronize()
+    return vals
 
 
 # FP32 lanes of the GB300 (152 SMs x 128) at the maximum SM clock: the issue peak of the blend

@@ -114,9 +114,23 @@ enum {
   V3DG_OPT_SPLIT_PAIRS = 6,  /* tiles with at least this many pairs are blended as four 8x8
                                 quadrants by separate blocks (default 16384; the image does not
                                 depend on it) */
-  V3DG_OPT_ATTR_FP16 = 7     /* 1: assets loaded from now on keep opacity and SH in float16 (rounded
+  V3DG_OPT_ATTR_FP16 = 7,    /* 1: assets loaded from now on keep opacity and SH in float16 (rounded
                                 to nearest even); means, scales and rotations stay float32 and all
                                 arithmetic stays float32 */
+  V3DG_OPT_SELECT_TOPDOWN = 8, /* 1: v3dg_select walks each instance's tree from its roots, level by
+                                level, testing only nodes whose parent's footprint exceeds tau_F and
+                                skipping subtrees that the visibility cull rejects as a whole; the
+                                cut is the same as the flat test of every node (F grows from a node
+                                to its parent, Sec. 3.4), in the same order.  Default 0 (flat). */
+  V3DG_OPT_BLEND_BATCH = 9,    /* records the blend stages per batch in shared memory: 128, 256
+                                (default) or 512; the image does not depend on it */
+  V3DG_OPT_GRAPHS = 10         /* 1: v3dg_select only stages the camera and instances, and
+                                v3dg_render runs the selection and the whole render as one CUDA
+                                graph, captured the first time a configuration (instance and view
+                                count, image size and intrinsics, buffer capacities, options,
+                                output pointers) is seen and replayed after that.  Same images;
+                                the frame counters are valid after v3dg_render.  Not used while
+                                V3DG_OPT_STAGE_TIMING is on.  Default 0. */
 };
 
 /* Create a context on CUDA device `device`.  `alloc` may be NULL (cudaMalloc/cudaFree). */
@@ -145,8 +159,19 @@ v3dg_status v3dg_set_instances(v3dg_ctx* ctx, uint32_t n, const uint32_t* asset_
  * F = pi r'^2 fx fy / z^2 of the own and parent spheres (Sec. 3.3, Fig. 4; r' = s_i r, +inf when
  * |z| <= r'), keep (i, n) iff F_c <= tau_F < F_p, with tau_F = float32(gaussians_per_group *
  * tau_px^2).  Clusters whose Gaussians provably cannot reach a pixel are dropped afterwards (this
- * changes no pixel).  Enqueued only; counters are available through v3dg_frame_stats. */
+ * changes no pixel).  Enqueued only; counters are available through v3dg_frame_stats.
+ * V3DG_EINVAL for an image of more than 2^20 16x16 tiles (above 16384 x 16384 pixels). */
 v3dg_status v3dg_select(v3dg_ctx* ctx, const v3dg_camera* cam, float tau_px);
+
+/* v3dg_select for n_views cameras at once (a batch of frames of the same instances): every stage
+ * of the following v3dg_render covers all views in one launch -- selection over (view, instance,
+ * cluster), one depth sort of every view's Gaussians, pairs keyed by (view, tile) -- and it writes
+ * n_views images one after the other (view v at offset v * height * width).  Each image is the one
+ * v3dg_select with that camera alone gives, bit for bit.  The cameras must share image size,
+ * intrinsics and near plane (V3DG_EINVAL otherwise); the views' tiles together are at most 2^20.
+ * The parity read-backs then report instance v * n_instances + i for instance i in view v, and
+ * v3dg_get_tile_ranges the (view, tile) ranges.  The paper renders one view at a time (Sec. 5). */
+v3dg_status v3dg_select_views(v3dg_ctx* ctx, const v3dg_camera* cams, uint32_t n_views, float tau_px);
 
 /* Splat the selected Gaussians (Sec. 2.1; Sec. 5.1: no 2D dilation): projection to 2D means and
  * conics, binning to 16x16 tiles, (tile, depth) sort with ties broken by Gaussian id, and per
@@ -156,6 +181,16 @@ v3dg_status v3dg_select(v3dg_ctx* ctx, const v3dg_camera* cam, float tau_px);
  * height * width float32 final transmittance, or NULL.  Requires a prior v3dg_select
  * (V3DG_ENOTFOUND otherwise). */
 v3dg_status v3dg_render(v3dg_ctx* ctx, float* rgb_out, float* T_out);
+
+/* Autotuner of the blend's batch size and work split.  Re-runs the blend stage of the last
+ * rendered frame (its sorted pairs and records are still on the device) with every combination of
+ * records per batch (128, 256, 512) and long-tile split threshold (4096, 16384, 65536 pairs, or
+ * none), times each with CUDA events (best of 3 after one warm-up run) and keeps the fastest as
+ * V3DG_OPT_BLEND_BATCH and V3DG_OPT_SPLIT_PAIRS for the frames that follow.  Neither changes the
+ * image.  Synchronous; the caller's image is not touched.  V3DG_ENOTFOUND without a rendered
+ * frame, V3DG_EOVERFLOW if that frame was not valid.  batch, split_pairs, best_ms: the choice and
+ * its time, each may be NULL.  The paper has no counterpart (its rasterizer is fixed). */
+v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* batch, uint32_t* split_pairs, float* best_ms);
 
 /* v3dg_render into HOST buffers (same layouts): the image is produced on the device and copied
  * back before the call returns. */

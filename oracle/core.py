@@ -249,8 +249,12 @@ class Projected:
     pix: np.ndarray          # (k, 4) float64 pixel range (x0, x1, y0, y1)
 
 
-def project(assets, inst, cam, cut: Cut) -> Projected:
-    """EWA projection of every Gaussian of the cut (Sec. 2.1, eps2d = 0 as Sec. 5.1 sets)."""
+def project(assets, inst, cam, cut: Cut, only=None) -> Projected:
+    """EWA projection of every Gaussian of the cut (Sec. 2.1, eps2d = 0 as Sec. 5.1 sets).
+
+    ``only``: optional {instance: asset-local Gaussian indices}; then only those Gaussians of the
+    cut are projected (each exactly as without it).
+    """
     m_all = compose(cam.world_to_cam, inst.rot, inst.trans, inst.scale)
     cam_c = cam.center
     fx, fy, cx, cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
@@ -268,6 +272,8 @@ def project(assets, inst, cam, cut: Cut) -> Projected:
         seg = np.repeat(np.arange(len(nodes)), cnt)
         off = np.concatenate([[0], np.cumsum(cnt)[:-1]])
         local = first[seg] + (np.arange(int(cnt.sum())) - off[seg])
+        if only is not None:
+            local = local[np.isin(local, only.get(int(i), np.zeros(0, np.int64)))]
         m = m_all[i]
         mu = a.means[local].astype(np.float64)
         view = mu @ m[:, :3].T + m[:, 3]
@@ -456,7 +462,8 @@ def nodes_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float =
         (1 + l_y^2)) / z_min (Frobenius bound, |x'/z| <= l_x, |y'/z| <= l_y), and the view-space
         covariance has largest eigenvalue (s sigma)^2, so the alpha >= 1/255 ellipse
         (q <= 2 ln(255 o) <= 2 ln 255) lies within sqrt(2 ln 255) ||J||_2 s sigma of the mean.
-    Nodes with z_min <= near are always kept.  The bound is widened by 2 px (the margin of
+    Nodes with z_min <= near are kept unless the whole ball lies behind the near plane (then the
+    projection culls all of their Gaussians).  The bound is widened by 2 px (the margin of
     render_pixels) plus ``slack_px``.
     """
     m_all = compose(cam.world_to_cam, inst.rot, inst.trans, inst.scale)
@@ -468,8 +475,11 @@ def nodes_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float =
     q = np.asarray([(px + 0.5, py + 0.5) for px, py in pixels], np.float64).reshape(-1, 2)
     balls = {}
     keep = np.zeros(len(cut.inst), bool)
+    by_inst = np.argsort(cut.inst, kind="stable")
+    inst_sorted = cut.inst[by_inst]
     for i in np.unique(cut.inst):
-        sel = np.nonzero(cut.inst == i)[0]
+        lo, hi = np.searchsorted(inst_sorted, [i, i + 1])
+        sel = by_inst[lo:hi]
         a_id = int(inst.asset[i])
         if a_id not in balls:
             balls[a_id] = node_mean_balls(assets[a_id])
@@ -487,11 +497,57 @@ def nodes_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float =
             spread = ksig * jn * s * sigma[nodes] / zmin + 2.0 + slack_px
             dx = fx * rv * np.sqrt(cv[:, 0] ** 2 + cv[:, 2] ** 2) / (cv[:, 2] * zmin) + spread
             dy = fy * rv * np.sqrt(cv[:, 1] ** 2 + cv[:, 2] ** 2) / (cv[:, 2] * zmin) + spread
-        hit = ~front
+        behind = cv[:, 2] + rv < float(cam.near)   # every mean behind the near plane: all culled
+        hit = ~front & ~behind
         for qx, qy in q:
             hit |= front & (np.abs(qx - ux) <= dx) & (np.abs(qy - uy) <= dy)
         keep[sel] = hit
     return Cut(cut.inst[keep], cut.node[keep], cut.ties)
+
+
+def gaussians_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float = 1.0):
+    """The Gaussians of the cut that can have alpha >= 1/255 at one of the pixels.
+
+    First the clusters (nodes_reaching_pixels), then each of their Gaussians by its own bound:
+    with its mean at view depth z > near and pixel position u, its alpha >= 1/255 ellipse lies
+    within sqrt(2 ln 255) ||J||_2 s sigma of u, ||J||_2 <= sqrt(f_x^2 (1 + l_x^2) + f_y^2
+    (1 + l_y^2)) / z and sigma = exp(its largest log-scale).  Gaussians with z <= near are kept.
+    Returns (the sub-cut of those clusters, {instance: sorted asset-local indices}) for project.
+    """
+    sub = nodes_reaching_pixels(assets, inst, cam, cut, pixels, slack_px)
+    m_all = compose(cam.world_to_cam, inst.rot, inst.trans, inst.scale)
+    fx, fy, cx, cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    limx = CLAMP_FOV * (0.5 * cam.width / fx)
+    limy = CLAMP_FOV * (0.5 * cam.height / fy)
+    jn = math.sqrt(fx * fx * (1.0 + limx * limx) + fy * fy * (1.0 + limy * limy))
+    ksig = math.sqrt(2.0 * math.log(255.0))
+    q = np.asarray([(px + 0.5, py + 0.5) for px, py in pixels], np.float64).reshape(-1, 2)
+    only = {}
+    by_inst = np.argsort(sub.inst, kind="stable")
+    inst_sorted = sub.inst[by_inst]
+    for i in np.unique(sub.inst):
+        lo, hi = np.searchsorted(inst_sorted, [i, i + 1])
+        nodes = np.sort(sub.node[by_inst[lo:hi]]).astype(np.int64)
+        a = assets[int(inst.asset[i])]
+        cnt = a.node_count[nodes].astype(np.int64)
+        start = np.cumsum(cnt) - cnt
+        local = np.repeat(a.node_first[nodes].astype(np.int64), cnt) + (np.arange(int(cnt.sum())) - np.repeat(start, cnt))
+        m = m_all[i]
+        s = float(inst.scale[i])
+        view = a.means[local].astype(np.float64) @ m[:, :3].T + m[:, 3]
+        z = view[:, 2]
+        front = z > float(cam.near)
+        sigma = np.exp(a.log_scales[local].astype(np.float64).max(axis=1))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = fx * view[:, 0] / z + cx
+            v = fy * view[:, 1] / z + cy
+            spread = ksig * jn * s * sigma / z + 2.0 + slack_px
+        hit = ~front
+        for qx, qy in q:
+            hit |= front & (np.abs(qx - u) <= spread) & (np.abs(qy - v) <= spread)
+        if hit.any():
+            only[int(i)] = local[hit]
+    return sub, only
 
 
 def render_image(p: Projected, width: int, height: int):

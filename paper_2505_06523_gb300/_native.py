@@ -22,6 +22,9 @@ V3DG_OPT_CAP_PAIRS = 4
 V3DG_OPT_COUNT_WORK = 5
 V3DG_OPT_SPLIT_PAIRS = 6
 V3DG_OPT_ATTR_FP16 = 7
+V3DG_OPT_SELECT_TOPDOWN = 8
+V3DG_OPT_BLEND_BATCH = 9
+V3DG_OPT_GRAPHS = 10
 
 
 class V3dgError(RuntimeError):
@@ -89,6 +92,7 @@ SIGNATURES = {
     "v3dg_load_hierarchy": (_I32, [_P, ctypes.POINTER(v3dg_hierarchy_desc), ctypes.POINTER(_U32)]),
     "v3dg_set_instances": (_I32, [_P, _U32, _P, _P, _P, _P]),
     "v3dg_select": (_I32, [_P, ctypes.POINTER(v3dg_camera), _F32]),
+    "v3dg_select_views": (_I32, [_P, ctypes.POINTER(v3dg_camera), _U32, _F32]),
     "v3dg_render": (_I32, [_P, _P, _P]),
     "v3dg_render_host": (_I32, [_P, _P, _P]),
     "v3dg_frame_stats": (_I32, [_P, ctypes.POINTER(v3dg_stats)]),
@@ -97,6 +101,7 @@ SIGNATURES = {
     "v3dg_get_pairs": (_I32, [_P, _U64, ctypes.POINTER(_U64), _P, _P, _P, _P]),
     "v3dg_get_tile_ranges": (_I32, [_P, _P, _U64, ctypes.POINTER(_U64)]),
     "v3dg_stage_times": (_I32, [_P, _P, _I32, ctypes.POINTER(_U64)]),
+    "v3dg_autotune_blend": (_I32, [_P, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_F32)]),
     "v3dg_sort_pairs": (_I32, [_P, _P, _P, _U64, _I32, _I32]),
     "v3dg_sort_pairs_noalloc": (_I32, [_P, _P, _U64, _I32, _I32, _P]),
     "v3dg_server_start": (_I32, [_P, _I32, _U64]),
@@ -171,6 +176,11 @@ def v3dg_select(ctx, cam: v3dg_camera, tau_px: float) -> None:
     _check(ctx, lib().v3dg_select(ctx, ctypes.byref(cam), float(tau_px)))
 
 
+def v3dg_select_views(ctx, cams: list, tau_px: float) -> None:
+    arr = (v3dg_camera * len(cams))(*cams)
+    _check(ctx, lib().v3dg_select_views(ctx, arr, len(cams), float(tau_px)))
+
+
 def v3dg_render(ctx, rgb_ptr: int, t_ptr: int | None) -> None:
     _check(ctx, lib().v3dg_render(ctx, _P(rgb_ptr), _P(t_ptr) if t_ptr else None))
 
@@ -217,6 +227,12 @@ def v3dg_stage_times(ctx, ms_ptr: int | None, n: int) -> int:
     launches = _U64()
     _check(ctx, lib().v3dg_stage_times(ctx, _P(ms_ptr) if ms_ptr else None, n, ctypes.byref(launches)))
     return launches.value
+
+
+def v3dg_autotune_blend(ctx) -> tuple[int, int, float]:
+    b, sp, ms = _U32(), _U32(), _F32()
+    _check(ctx, lib().v3dg_autotune_blend(ctx, ctypes.byref(b), ctypes.byref(sp), ctypes.byref(ms)))
+    return int(b.value), int(sp.value), float(ms.value)
 
 
 def v3dg_sort_pairs(ctx, keys_ptr: int, vals_ptr: int, n: int, begin_bit: int, end_bit: int) -> None:

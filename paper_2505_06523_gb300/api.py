@@ -129,25 +129,36 @@ class Context:
     # -- frame
     def select(self, cam, tau_px: float):
         self.cam = cam
+        self.n_views = 1
         N.v3dg_select(self.ctx, camera_struct(cam), float(tau_px))
 
+    def select_views(self, cams, tau_px: float):
+        """Several cameras (same image size and intrinsics) in one batch of launches; the next
+        render returns (n_views, h, w, 3)."""
+        self.cam = cams[0]
+        self.n_views = len(cams)
+        N.v3dg_select_views(self.ctx, [camera_struct(c) for c in cams], float(tau_px))
+
     def render(self, rgb=None, T=None, want_T: bool = False):
-        """Render into torch tensors on the device; returns (rgb (h, w, 3), T (h, w) or None)."""
+        """Render into torch tensors on the device; returns (rgb (h, w, 3), T (h, w) or None), or
+        (n_views, h, w, 3) and (n_views, h, w) after select_views."""
         torch = self._torch
         h, w = int(self.cam.height), int(self.cam.width)
+        lead = (self.n_views,) if getattr(self, "n_views", 1) > 1 else ()
         if rgb is None:
-            rgb = torch.empty((h, w, 3), dtype=torch.float32, device=self.device)
+            rgb = torch.empty(lead + (h, w, 3), dtype=torch.float32, device=self.device)
         if T is None and want_T:
-            T = torch.empty((h, w), dtype=torch.float32, device=self.device)
+            T = torch.empty(lead + (h, w), dtype=torch.float32, device=self.device)
         N.v3dg_render(self.ctx, rgb.data_ptr(), T.data_ptr() if T is not None else None)
         return rgb, T
 
     def render_host(self, rgb: np.ndarray | None = None, T: np.ndarray | None = None, want_T: bool = False):
         h, w = int(self.cam.height), int(self.cam.width)
+        lead = (self.n_views,) if getattr(self, "n_views", 1) > 1 else ()
         if rgb is None:
-            rgb = np.empty((h, w, 3), np.float32)
+            rgb = np.empty(lead + (h, w, 3), np.float32)
         if T is None and want_T:
-            T = np.empty((h, w), np.float32)
+            T = np.empty(lead + (h, w), np.float32)
         N.v3dg_render_host(self.ctx, rgb.ctypes.data, T.ctypes.data if T is not None else None)
         return rgb, T
 
@@ -192,6 +203,12 @@ class Context:
         if n:
             N.v3dg_get_tile_ranges(self.ctx, out.ctypes.data, n)
         return out
+
+    def autotune_blend(self) -> dict:
+        """Time the last frame's blend with every batch size and split threshold and keep the
+        fastest (v3dg_autotune_blend)."""
+        b, sp, ms = N.v3dg_autotune_blend(self.ctx)
+        return {"batch": b, "split_pairs": sp, "ms": ms}
 
     # -- the sort on its own
     # -- serving

@@ -2,15 +2,18 @@
 //
 // The Gaussians arrive sorted by depth (stage one of the two-stage (tile, depth) sort), so the
 // pairs are emitted in depth order; a stable sort on the tile id then yields (tile, depth, id)
-// order, and each tile's range of the sorted pairs is found by boundary detection.
+// order, and each tile's range of the sorted pairs is found by boundary detection.  A pair key
+// carries, above the 20-bit tile id, the Gaussian's pixel box clipped to that tile (so that the
+// blend can skip pairs by their keys alone).
 #include "dev_common.cuh"
 
 namespace v3dg {
 namespace {
 
-__device__ __forceinline__ uint32_t rect_area(const uint2 r) {
-  const uint32_t w = (r.x >> 16) - (r.x & 0xFFFFu) + 1u;
-  const uint32_t h = (r.y >> 16) - (r.y & 0xFFFFu) + 1u;
+// Tiles covered by a Gaussian's pixel box (x0 | x1 << 16, y0 | y1 << 16, inclusive pixels).
+__device__ __forceinline__ uint32_t rect_area(const uint2 b) {
+  const uint32_t w = ((b.x >> 16) >> 4) - ((b.x & 0xFFFFu) >> 4) + 1u;
+  const uint32_t h = ((b.y >> 16) >> 4) - ((b.y & 0xFFFFu) >> 4) + 1u;
   return w * h;
 }
 
@@ -23,11 +26,13 @@ constexpr int kExpThreads = 256, kExpItems = 4, kExpTile = kExpThreads * kExpIte
 // writes are contiguous.
 __global__ void __launch_bounds__(kExpThreads)
 k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uint32_t cap, uint32_t cap_pairs,
-         int tiles_x, uint32_t* __restrict__ pk, uint32_t* __restrict__ pv, uint32_t* __restrict__ frame,
-         uint32_t tc_slot, uint64_t* __restrict__ status, uint32_t epoch) {
+         int tiles_x, const uint2* __restrict__ list, uint32_t inst_per_view, uint32_t tiles_per_view,
+         uint32_t* __restrict__ pk, uint32_t* __restrict__ pv, uint32_t* __restrict__ frame, uint32_t tc_slot,
+         uint64_t* __restrict__ status, uint32_t epoch) {
   __shared__ uint32_t s_off[kExpTile + 1];
   __shared__ uint2 s_rect[kExpTile];
   __shared__ uint32_t s_slot[kExpTile];
+  __shared__ uint32_t s_tbase[kExpTile];   // first (view, tile) id of the Gaussian's view
   __shared__ uint32_t s_scan[kExpThreads / 32 + 1];
   __shared__ uint32_t s_tile, s_base;
   if (threadIdx.x == 0) s_tile = atomicAdd(frame + kTileCounters + tc_slot, 1u);
@@ -48,6 +53,7 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
       const uint2 r = rect[slot];
       s_slot[j] = slot;
       s_rect[j] = r;
+      s_tbase[j] = inst_per_view ? (list[slot / kSlots].x / inst_per_view) * tiles_per_view : 0u;
       c[i] = rect_area(r);
     }
     sum += c[i];
@@ -78,11 +84,16 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
       if (s_off[mid] <= p) lo = mid; else hi = mid;
     }
     const uint2 r = s_rect[lo];
-    const uint32_t tx0 = r.x & 0xFFFFu, tx1 = r.x >> 16, ty0 = r.y & 0xFFFFu;
-    const uint32_t w = tx1 - tx0 + 1u;
+    const uint32_t x0 = r.x & 0xFFFFu, x1 = r.x >> 16, y0 = r.y & 0xFFFFu, y1 = r.y >> 16;
+    const uint32_t tx0 = x0 >> 4, ty0 = y0 >> 4;
+    const uint32_t w = (x1 >> 4) - tx0 + 1u;
     const uint32_t k = p - s_off[lo];
     const uint32_t dy = k / w;
-    pk[base + p] = (ty0 + dy) * uint32_t(tiles_x) + tx0 + (k - dy * w);
+    const uint32_t tx = tx0 + (k - dy * w), ty = ty0 + dy;
+    // above the tile id: the box clipped to this tile, tile-local (rows exact, columns in quads)
+    const uint32_t bx0 = x0 > 16 * tx ? x0 - 16 * tx : 0u, bx1 = min(x1 - 16 * tx, 15u);
+    const uint32_t by0 = y0 > 16 * ty ? y0 - 16 * ty : 0u, by1 = min(y1 - 16 * ty, 15u);
+    pk[base + p] = (s_tbase[lo] + ty * uint32_t(tiles_x) + tx) | (by0 << 20) | (by1 << 24) | ((bx0 >> 2) << 28) | ((bx1 >> 2) << 30);
     pv[base + p] = s_slot[lo];
   }
 }
@@ -98,21 +109,23 @@ k_ranges(const uint32_t* __restrict__ tk, uint32_t cap_pairs, const uint32_t* __
          uint2* __restrict__ ranges, uint32_t n_tiles) {
   const uint32_t n = min(frame[kPairsEff], cap_pairs);
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const uint32_t t = tk[k];
+    const uint32_t t = tk[k] & kPairTileMask;
     if (t >= n_tiles) continue;
-    if (k == 0 || tk[k - 1] != t) ranges[t].x = k;
-    if (k + 1 == n || tk[k + 1] != t) ranges[t].y = k + 1;
+    if (k == 0 || (tk[k - 1] & kPairTileMask) != t) ranges[t].x = k;
+    if (k + 1 == n || (tk[k + 1] & kPairTileMask) != t) ranges[t].y = k + 1;
   }
 }
 
 }  // namespace
 
 cudaError_t launch_expand(const uint32_t* slots, const uint2* rect, uint32_t cap, uint32_t cap_pairs, int tiles_x,
-                          uint32_t* pk, uint32_t* pv, uint32_t* frame, uint32_t tc_slot, uint64_t* status,
-                          uint32_t epoch, cudaStream_t st) {
+                          const uint2* list, uint32_t inst_per_view, uint32_t tiles_per_view, uint32_t* pk,
+                          uint32_t* pv, uint32_t* frame, uint32_t tc_slot, uint64_t* status, uint32_t epoch,
+                          cudaStream_t st) {
   const uint32_t blocks = (cap + kExpTile - 1) / kExpTile;
-  if (blocks) k_expand<<<blocks, kExpThreads, 0, st>>>(slots, rect, cap, cap_pairs, tiles_x, pk, pv, frame, tc_slot,
-                                                       status, epoch);
+  if (blocks)
+    k_expand<<<blocks, kExpThreads, 0, st>>>(slots, rect, cap, cap_pairs, tiles_x, list, inst_per_view, tiles_per_view,
+                                             pk, pv, frame, tc_slot, status, epoch);
   k_pairs_eff<<<1, 1, 0, st>>>(frame, cap_pairs);
   return cudaGetLastError();
 }

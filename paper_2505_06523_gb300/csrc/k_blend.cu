@@ -12,8 +12,9 @@
 //    stopping before T (1 - a) < 1e-4.
 // So sequential work is spent only where a Gaussian contributes, and small Gaussians (a few
 // pixels each) no longer occupy whole warps.  Records are staged through shared memory; a batch
-// is filled only with records whose box reaches a row pair that still has an unfinished pixel,
-// scanning ahead in the list by their boxes alone.  Each record's mean is stored relative to the
+// is filled only with records whose box holds a pixel that is still accumulating, found by
+// scanning ahead in the sorted pair keys, which carry each Gaussian's box within the tile (so
+// skipped records cost one coalesced 4-byte read).  Each record's mean is stored relative to the
 // pixel origin of its first tile, so dx, dy are differences of small numbers.
 #include <algorithm>
 
@@ -24,9 +25,6 @@ namespace {
 
 constexpr int kBlendThreads = 256;
 constexpr int kBlendWarps = kBlendThreads / 32;
-constexpr int kBatch = 256;                    // records staged per batch
-constexpr int kPer = kBatch / kBlendThreads;   // consecutive records staged per thread
-constexpr int kMaskWords = kBatch / 32;        // per-pixel mask words
 constexpr float kLog2MinAlpha = -7.9943534f;  // log2(1/255)
 
 // log2(alpha) of a staged record at tile-local pixel centre (fx, fy); one definition for both phases
@@ -35,7 +33,18 @@ __device__ __forceinline__ float log2_alpha(const float4 g, const float4 c, floa
   return fmaf(dx, fmaf(g.z, dx, g.w * dy), fmaf(c.x * dy, dy, c.y));
 }
 
-// Column / row masks of a record's pixel box in tile (tx, ty) and its clipped extent.
+// True when the box that a pair key carries (see kPairTileMask: rows y0..y1, column quads
+// q0..q1) holds a pixel whose bit is set in `live` (one word per row pair: row 2w in bits
+// 0..15, row 2w + 1 in 16..31).
+__device__ __forceinline__ bool box_live(uint32_t key, const uint32_t* live) {
+  const uint32_t y0 = (key >> 20) & 15u, y1 = (key >> 24) & 15u, q0 = (key >> 28) & 3u, q1 = key >> 30;
+  const uint32_t cols = (0xFFFFu >> (12u - 4u * q1)) & (0xFFFFu << (4u * q0));
+  for (uint32_t y = y0; y <= y1; ++y)
+    if ((live[y >> 1] >> ((y & 1u) * 16u)) & cols) return true;
+  return false;
+}
+
+// A record's pixel box (from its third float4) clipped to tile (tx, ty), tile-local.
 __device__ __forceinline__ void box_in_tile(const float4 r2, int tx, int ty, int* x0, int* x1, int* y0, int* y1) {
   const uint32_t bx = __float_as_uint(r2.z), by = __float_as_uint(r2.w);
   *x0 = max(int(bx & 0xFFFFu) - 16 * tx, 0);
@@ -44,33 +53,36 @@ __device__ __forceinline__ void box_in_tile(const float4 r2, int tx, int ty, int
   *y1 = min(int(by >> 16) - 16 * ty, 15);
 }
 
-// Row-pair mask of a record's box: bit w when it reaches rows 2w, 2w + 1 of the tile.
-__device__ __forceinline__ uint32_t rowpair_mask(int y0, int y1) {
-  if (y0 > y1) return 0u;
-  const int w0 = y0 >> 1, w1 = y1 >> 1;
-  return ((0xFFu >> (7 - w1)) & (0xFFu << w0)) & 0xFFu;
-}
+// Resident blocks per SM: batches of 128 records keep shared memory (10 KB) and registers (40)
+// small enough for 6 blocks, the larger ones run 4.
+constexpr int blend_blocks_per_sm(int batch) { return batch == 128 ? 6 : 4; }
 
-template <bool kCount>
-__global__ void __launch_bounds__(kBlendThreads, 4)
+// kBatch: records staged per batch (128, 256 or 512; the image does not depend on it).
+template <bool kCount, int kBatch>
+__global__ void __launch_bounds__(kBlendThreads, blend_blocks_per_sm(kBatch))
 k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, const uint32_t* __restrict__ n_items,
-        uint32_t* __restrict__ tile_counter, const uint32_t* __restrict__ pv, const float4* __restrict__ rec, uint32_t cap_slots, int width,
-        int height, int tiles_x, float* __restrict__ rgb, float* __restrict__ t_out,
+        uint32_t* __restrict__ tile_counter, const uint32_t* __restrict__ tk, const uint32_t* __restrict__ pv,
+        const float4* __restrict__ rec, uint32_t cap_slots, int width,
+        int height, int tiles_x, int tiles_per_view, float* __restrict__ rgb, float* __restrict__ t_out,
         unsigned long long* __restrict__ work, const uint32_t* __restrict__ frame, uint32_t* __restrict__ sticky) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (frame[kOverflow]) atomicOr(sticky, 1u);
     if (frame[kTimeout]) atomicOr(sticky + 1, 1u);
   }
+  constexpr int kPer = kBatch >= kBlendThreads ? kBatch / kBlendThreads : 1;   // records staged per thread
+  constexpr int kMaskWords = kBatch / 32;                                       // per-pixel mask words
+  static_assert(kBatch % 32 == 0 && (kBatch <= kBlendThreads || kBatch % kBlendThreads == 0), "batch size");
   __shared__ float4 s_g[kBatch];                    // (u, v, na, nb) in this tile's pixel frame
   __shared__ float4 s_c[kBatch];                    // (nc, log2 o, r, g)
   __shared__ float s_b[kBatch];                     // b
   __shared__ uint32_t s_box[kBatch];                // clipped box: x0 | x1 << 8 | y0 << 16 | y1 << 24
   __shared__ uint32_t s_eoff[kBatch + 1];           // exclusive prefix of the box areas
   __shared__ uint32_t s_mask[kBlendThreads][kMaskWords];  // [pixel][record word]: contributing records
-  __shared__ uint32_t s_done[kBlendWarps];          // finished pixels, one word per row pair
-  __shared__ uint32_t s_qslot[kBatch];              // a filtered batch: slots of the records, in order
+  __shared__ uint32_t s_live[kBlendWarps];          // unfinished pixels of the item, one word per row pair
+  __shared__ uint32_t s_qslot[kBatch];              // the batch: slots of its records, in list order
+  __shared__ uint32_t s_cnt[32];
   __shared__ uint32_t s_scan[kBlendWarps + 1];
-  __shared__ uint32_t s_next, s_resume;
+  __shared__ uint32_t s_next, s_resume, s_total;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;   // this thread's pixel in the tile
   const float fx = float(lx) + 0.5f, fy = float(ly) + 0.5f;
@@ -84,8 +96,9 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
     __syncthreads();
     if (next >= *n_items) break;
     const uint32_t item = items[next];
-    const int tile = int(item & 0xFFFFFFu), region = int(item >> 24);
-    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int tile = int(item & 0xFFFFFFu), region = int(item >> 24);   // (view, tile) id
+    const int view = tile / tiles_per_view, vt = tile - view * tiles_per_view;
+    const int tx = vt % tiles_x, ty = vt / tiles_x;
     // the item's pixel rectangle within the tile: the whole tile or one 8x8 quadrant
     const int qx0 = region ? 8 * ((region - 1) & 1) : 0, qy0 = region ? 8 * ((region - 1) >> 1) : 0;
     const int qx1 = region ? qx0 + 7 : 15, qy1 = region ? qy0 + 7 : 15;
@@ -97,68 +110,76 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
     bool done = !inside;
     uint32_t sp = range.x;   // next list position to look at (uniform across the block)
     for (;;) {
-      // row pairs (one warp each) that still have an unfinished pixel
+      // the item's unfinished pixels, one word per row pair (row 2w: bits 0..15, row 2w + 1: 16..31)
       const uint32_t dword = __ballot_sync(0xffffffffu, done);
-      if (lane == 0) s_done[warp] = dword;
+      if (lane == 0) s_live[warp] = ~dword;
       __syncthreads();
-      uint32_t act = 0;
+      uint32_t any_live = 0;
 #pragma unroll
-      for (int w = 0; w < kBlendWarps; ++w) act |= uint32_t(s_done[w] != 0xffffffffu) << w;
-      if (act == 0 || sp >= range.y) break;
-      // the batch: the next kBatch records of the list when every row pair is live, else the next
-      // records whose box reaches a live row pair of the item, in list order
+      for (int w = 0; w < kBlendWarps; ++w) any_live |= s_live[w];
+      if (any_live == 0 || sp >= range.y) break;
+      // the batch: the next records of the list whose box (carried by the pair key) holds an
+      // unfinished pixel, in list order; kScan * 256 consecutive keys per step
       uint32_t q = 0;
-      const bool all_live = region == 0 && act == (1u << kBlendWarps) - 1u;
-      if (all_live) {
-        q = min(uint32_t(kBatch), range.y - sp);
-      } else {
-        while (q < uint32_t(kBatch) && sp < range.y) {
-          constexpr int kScan = 4;   // records tested per thread and step
-          const uint32_t i0 = sp + threadIdx.x * kScan;
-          uint32_t sl[kScan], hits = 0;
+      while (q < uint32_t(kBatch) && sp < range.y) {
+        constexpr int kScan = 4;
+        uint32_t key[kScan], ball[kScan], hits = 0;
 #pragma unroll
-          for (int k = 0; k < kScan; ++k) {
-            sl[k] = 0xFFFFFFFFu;
-            if (i0 + k < range.y) {
-              sl[k] = pv[i0 + k];
-              if (sl[k] < cap_slots) {
-                int x0, x1, y0, y1;
-                box_in_tile(rec[3 * size_t(sl[k]) + 2], tx, ty, &x0, &x1, &y0, &y1);
-                if (x0 <= qx1 && x1 >= qx0 && y0 <= qy1 && y1 >= qy0 && (rowpair_mask(y0, y1) & act))
-                  hits |= 1u << k;
-              }
-            }
+        for (int k = 0; k < kScan; ++k) {
+          const uint32_t pos = sp + k * kBlendThreads + threadIdx.x;
+          key[k] = 0;
+          if (pos < range.y) {
+            key[k] = tk[pos];
+            if (box_live(key[k], s_live)) hits |= 1u << k;
           }
-          uint32_t total;
-          uint32_t pos = q + block_exclusive_scan<kBlendWarps>(__popc(hits), s_scan, &total);
+          ball[k] = __ballot_sync(0xffffffffu, (hits >> k) & 1u);
+          if (lane == 0) s_cnt[k * kBlendWarps + warp] = __popc(ball[k]);
+        }
+        __syncthreads();
+        if (warp == 0) {   // exclusive scan over (step, warp) = list order
+          const uint32_t v = s_cnt[lane];
+          uint32_t incl = v;
 #pragma unroll
-          for (int k = 0; k < kScan; ++k) {
-            if ((hits >> k) & 1u) {
-              if (pos < uint32_t(kBatch)) s_qslot[pos] = sl[k];
-              else if (pos == uint32_t(kBatch)) s_resume = i0 + k;   // first record left over
-              ++pos;
-            }
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
           }
-          __syncthreads();
-          if (q + total > uint32_t(kBatch)) {
-            sp = s_resume;
-            q = kBatch;
-          } else {
-            sp = min(sp + uint32_t(kBlendThreads * kScan), range.y);
-            q += total;
+          s_cnt[lane] = incl - v;
+          if (lane == 31) s_total = incl;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScan; ++k) {
+          if ((hits >> k) & 1u) {
+            const uint32_t pos = sp + k * kBlendThreads + threadIdx.x;
+            const uint32_t idx = q + s_cnt[k * kBlendWarps + warp] + __popc(ball[k] & lanemask_lt());
+            if (idx < uint32_t(kBatch)) {
+              s_qslot[idx] = pv[pos];
+            } else if (idx == uint32_t(kBatch)) {
+              s_resume = pos;   // the first record left over
+            }
           }
         }
         __syncthreads();
-        if (q == 0) break;
+        const uint32_t total = s_total;
+        if (q + total > uint32_t(kBatch)) {
+          sp = s_resume;
+          q = kBatch;
+        } else {
+          sp = min(sp + uint32_t(kBlendThreads * kScan), range.y);
+          q += total;
+        }
+        static_assert(kScan * kBlendWarps == 32, "one scan lane per (step, warp)");
       }
-      // stage the batch (kPer consecutive records per thread); each record's clipped box area
+      if (q == 0) break;
+      // stage the batch (kPer consecutive records per thread); each record's box within the item
       uint32_t area[kPer], asum = 0;
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
         const uint32_t i = threadIdx.x * kPer + k;
         area[k] = 0;
         if (i < q) {
-          const uint32_t slot = all_live ? pv[sp + i] : s_qslot[i];
+          const uint32_t slot = s_qslot[i];
           if (slot < cap_slots) {
             const float4* r = rec + 3 * size_t(slot);
             const float4 r0 = r[0], r1 = r[1], r2 = r[2];
@@ -178,12 +199,11 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
         }
         asum += area[k];
       }
-      if (all_live) sp += q;
       uint32_t n_pairs;
       uint32_t eoff = block_exclusive_scan<kBlendWarps>(asum, s_scan, &n_pairs);
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {   // records q.. have area 0, so s_eoff[q] = n_pairs
-        s_eoff[threadIdx.x * kPer + k] = eoff;
+        if (threadIdx.x * kPer + k < uint32_t(kBatch)) s_eoff[threadIdx.x * kPer + k] = eoff;
         eoff += area[k];
       }
       if (threadIdx.x == 0) s_eoff[kBatch] = n_pairs;
@@ -217,7 +237,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
             const float4 g = s_g[j], c = s_c[j];
             const uint32_t bit = 1u << (j & 31);
             for (; e < stop; ++e) {
-              if (!((s_done[yy >> 1] >> ((yy & 1) * 16 + xx)) & 1u)) {   // pixel still accumulating
+              if ((s_live[yy >> 1] >> ((yy & 1) * 16 + xx)) & 1u) {   // pixel still accumulating
                 const float l2a = log2_alpha(g, c, float(xx) + 0.5f, float(yy) + 0.5f);
                 if (kCount) ++n_eval;
                 if (l2a >= kLog2MinAlpha && fminf(0.999f, exp2f(l2a)) >= 1.f / 255.f)
@@ -262,7 +282,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
       __syncthreads();
     }
     if (inside) {   // this item's pixels only
-      const size_t p = size_t(py) * width + px;
+      const size_t p = (size_t(view) * height + py) * width + px;
       rgb[3 * p + 0] = cr;
       rgb[3 * p + 1] = cg;
       rgb[3 * p + 2] = cb;
@@ -324,28 +344,60 @@ __global__ void __launch_bounds__(1024) k_blend_items(const uint2* __restrict__ 
 
 }  // namespace
 
-cudaError_t launch_blend(const uint2* ranges, uint32_t* items, uint32_t* tile_counter, const uint32_t* pv,
-                         const float4* rec, uint32_t cap_slots, const CamConst& cam, float* rgb, float* t_out,
-                         unsigned long long* work, const uint32_t* frame, uint32_t* sticky, uint32_t split_pairs,
-                         int sm_count, cudaStream_t st) {
-  const int n_tiles = cam.tiles_x * cam.tiles_y;
-  if (n_tiles == 0) return cudaSuccess;
-  uint32_t* n_items = items + 4 * size_t(n_tiles);
-  static const bool carveout_set = [] {   // 4 blocks of 41 KB per SM want the largest carveout
-    cudaFuncSetAttribute(k_blend<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(k_blend<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    return true;
-  }();
-  (void)carveout_set;
-  k_blend_items<<<1, 1024, 0, st>>>(ranges, n_tiles, split_pairs, items, n_items);
-  const int grid = std::min(4 * n_tiles, sm_count * 4);   // 4 resident blocks per SM (56 registers)
+namespace {
+
+template <int kBatch>
+void blend_launch(int grid, cudaStream_t st, const uint2* ranges, const uint32_t* items, const uint32_t* n_items,
+                  uint32_t* tile_counter, const uint32_t* tk, const uint32_t* pv, const float4* rec, uint32_t cap_slots,
+                  const CamConst& cam, float* rgb, float* t_out, unsigned long long* work, const uint32_t* frame,
+                  uint32_t* sticky) {
   if (work)
-    k_blend<true><<<grid, kBlendThreads, 0, st>>>(ranges, items, n_items, tile_counter, pv, rec, cap_slots,
-                                                  cam.width, cam.height, cam.tiles_x, rgb, t_out, work, frame, sticky);
+    k_blend<true, kBatch><<<grid, kBlendThreads, 0, st>>>(ranges, items, n_items, tile_counter, tk, pv, rec, cap_slots,
+                                                          cam.width, cam.height, cam.tiles_x, cam.tiles_x * cam.tiles_y, rgb,
+                                                          t_out, work, frame,
+                                                          sticky);
   else
-    k_blend<false><<<grid, kBlendThreads, 0, st>>>(ranges, items, n_items, tile_counter, pv, rec, cap_slots,
-                                                   cam.width, cam.height, cam.tiles_x, rgb, t_out, nullptr, frame,
-                                                   sticky);
+    k_blend<false, kBatch><<<grid, kBlendThreads, 0, st>>>(ranges, items, n_items, tile_counter, tk, pv, rec,
+                                                           cap_slots, cam.width, cam.height, cam.tiles_x,
+                                                           cam.tiles_x * cam.tiles_y, rgb, t_out,
+                                                           nullptr, frame, sticky);
+}
+
+}  // namespace
+
+cudaError_t blend_set_attributes() {
+  // 4 resident blocks of 11-43 KB shared memory per SM want the largest carveout
+  const void* fns[] = {(const void*)k_blend<true, 128>, (const void*)k_blend<false, 128>,
+                       (const void*)k_blend<true, 256>, (const void*)k_blend<false, 256>,
+                       (const void*)k_blend<true, 512>, (const void*)k_blend<false, 512>};
+  for (const void* f : fns) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                               cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_blend(const uint2* ranges, uint32_t* items, uint32_t* tile_counter, const uint32_t* tk,
+                         const uint32_t* pv, const float4* rec, uint32_t cap_slots, const CamConst& cam, float* rgb,
+                         float* t_out, unsigned long long* work, const uint32_t* frame, uint32_t* sticky,
+                         uint32_t split_pairs, int batch, int n_views, int sm_count, cudaStream_t st) {
+  const int n_tiles = cam.tiles_x * cam.tiles_y * n_views;
+  if (n_tiles == 0) return cudaSuccess;
+  if (batch != 128 && batch != 256 && batch != 512) return cudaErrorInvalidValue;
+  uint32_t* n_items = items + 4 * size_t(n_tiles);
+  k_blend_items<<<1, 1024, 0, st>>>(ranges, n_tiles, split_pairs, items, n_items);
+  const int per_sm = blend_blocks_per_sm(batch);
+  const int grid = std::min(4 * n_tiles, sm_count * per_sm);   // persistent: the resident blocks
+  if (batch == 128)
+    blend_launch<128>(grid, st, ranges, items, n_items, tile_counter, tk, pv, rec, cap_slots, cam, rgb, t_out, work,
+                      frame, sticky);
+  else if (batch == 256)
+    blend_launch<256>(grid, st, ranges, items, n_items, tile_counter, tk, pv, rec, cap_slots, cam, rgb, t_out, work,
+                      frame, sticky);
+  else
+    blend_launch<512>(grid, st, ranges, items, n_items, tile_counter, tk, pv, rec, cap_slots, cam, rgb, t_out, work,
+                      frame, sticky);
   return cudaGetLastError();
 }
 

@@ -7,7 +7,7 @@
 // k_project: one warp per render-list node (<= 64 Gaussians, 2 per lane), attribute-major loads
 //   (each cluster's attributes are one contiguous block of planes of 64 floats, so every warp load
 //   is one 128-byte line and a cluster's data is one region of memory).
-//   Writes a 48-byte blend record, the tile rectangle and the float32 depth key per Gaussian;
+//   Writes a 48-byte blend record, the pixel box and the float32 depth key per Gaussian;
 //   culled slots get the key 0xFFFFFFFF so that the depth sort moves them behind all visible ones.
 #include <cuda_fp16.h>
 
@@ -172,7 +172,7 @@ __device__ __forceinline__ uint32_t project_node(int lane, uint32_t ci, uint32_t
       keys[slot] = 0xFFFFFFFFu;
       continue;
     }
-    const int tx0 = int(x0) >> 4, tx1 = int(x1) >> 4, ty0 = int(y0) >> 4, ty1 = int(y1) >> 4;
+    const int tx0 = int(x0) >> 4, ty0 = int(y0) >> 4;
     // mean relative to the first tile's pixel origin (exact subtraction of the integer part)
     const float u_rel = (r0.x - float(16 * tx0)) + (r0.y + corr_u);
     const float v_rel = (r0.z - float(16 * ty0)) + (r0.w + corr_v);
@@ -211,7 +211,7 @@ __device__ __forceinline__ uint32_t project_node(int lane, uint32_t ci, uint32_t
     rp[1] = make_float4(-0.5f * kLog2e * ic, log2f(op), rgb[0], rgb[1]);
     rp[2] = make_float4(rgb[2], __uint_as_float(origin), __uint_as_float(uint32_t(x0) | (uint32_t(x1) << 16)),
                         __uint_as_float(uint32_t(y0) | (uint32_t(y1) << 16)));
-    rect[slot] = make_uint2(uint32_t(tx0) | (uint32_t(tx1) << 16), uint32_t(ty0) | (uint32_t(ty1) << 16));
+    rect[slot] = make_uint2(uint32_t(x0) | (uint32_t(x1) << 16), uint32_t(y0) | (uint32_t(y1) << 16));
     keys[slot] = __float_as_uint(z32);
     ++nvis;
   }

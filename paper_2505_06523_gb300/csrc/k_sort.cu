@@ -207,6 +207,15 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
 
 }  // namespace
 
+cudaError_t sort_set_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
 cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
                         uint32_t cap, int begin_bit, int end_bit, bool implicit_vals, const SortScratch& sc,
                         uint32_t* err_flag, uint32_t& epoch, int sm_count, cudaStream_t st, bool* result_in_1,
@@ -222,12 +231,6 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
   k_hist<<<sm_count * 4, 256, 0, st>>>(k0, n_dev, cap, begin_bit, end_bit, passes, sc.hist);
   k_hist_scan<<<1, kBins, 0, st>>>(sc.hist, passes, sc.hist + 4 * kBins);
   *launches += 2;
-  static const bool carveout_set = [] {   // once per process (thread-safe static initialisation)
-    cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    return true;
-  }();
-  (void)carveout_set;
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int p = 0; p < passes; ++p) {
     const int shift = begin_bit + 8 * p;

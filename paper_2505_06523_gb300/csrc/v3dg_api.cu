@@ -43,7 +43,9 @@ struct AssetHost {
   uint32_t n_gauss = 0, n_nodes = 0, sh_coeffs = 0, gpg = 0;
   bool half_color = false;
   std::vector<uint32_t> node_first;
+  uint32_t levels = 0;     // largest node level + 1
   DevBuf own, par, bound, sigma, flags, cnt, attr;
+  DevBuf child_off, child_list, sub_bound, sub_sigma;   // top-down selection
 };
 
 constexpr uint32_t kInitNodes = 1u << 14;
@@ -72,7 +74,9 @@ struct Pipe {
   v3dg_camera cam{};
   float tau_px = 0.f;
   CamConst cc{};
-  uint32_t n_inst_frame = 0;
+  uint32_t n_inst_frame = 0;   // instance frames of the selection: n_views * instances
+  uint32_t n_views = 1;        // cameras of the current frame (same intrinsics and image size)
+  int color_formats = 1;       // colour storage formats of the current instances' assets (bit 0 FP32, bit 1 FP16)
   int node_blocks = 0;
 
   DevBuf d_inst;
@@ -87,9 +91,17 @@ struct Pipe {
   DevBuf d_list, d_ref, d_keys0, d_keys1, d_vals0, d_vals1, d_rec, d_rect;
   DevBuf d_pk0, d_pk1, d_pv0, d_pv1, d_ranges, d_status, d_hist, d_cut;
   DevBuf d_img, d_timg, d_sort_k, d_sort_v, d_order;
+  DevBuf d_front0, d_front1, d_tdcount, d_bitmap;   // top-down selection
   bool depth_in1 = false, tiles_in1 = false;
   uint32_t epoch = 1;
   cudaEvent_t ev[kStages + 1] = {};
+  // CUDA-graph frames (V3DG_OPT_GRAPHS): the selection is enqueued with the render, and both are
+  // captured once per configuration (gkey) on cap_stream, then replayed on `stream`
+  bool select_pending = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint64_t> gkey;
+  uint64_t glaunches = 0;   // kernel launches in the captured graph
 };
 
 struct v3dg_ctx {
@@ -103,18 +115,14 @@ struct v3dg_ctx {
   bool sync_check = true, stage_timing = false, count_work = false;
   uint32_t split_pairs = 16384;
   bool attr_fp16 = false;   // store opacity and SH of the next loaded assets as float16
+  bool topdown = false;     // select level by level from the roots (same cut as the flat kernel)
+  int blend_batch = 256;    // records staged per blend batch: 128, 256 or 512
+  bool graphs = false;      // capture each frame's launches once and replay them as a CUDA graph
   Pipe main;
   Server* server = nullptr;
 };
 
 namespace {
-
-// Colour storage formats among the loaded assets: bit 0 float32, bit 1 float16.
-int color_formats(const v3dg_ctx* ctx) {
-  int f = 0;
-  for (const AssetHost& a : ctx->assets) f |= a.half_color ? 2 : 1;
-  return f;
-}
 
 v3dg_status fail(Pipe* c, v3dg_status s, const char* fmt, ...) {
   char buf[512];
@@ -242,7 +250,7 @@ void stage_event(Pipe* c, int i) {
 
 // ------------------------------------------------------------------ per-frame set-up (FP64, host)
 
-v3dg_status setup_frame(Pipe* c, const v3dg_camera* cam, float tau_px) {
+v3dg_status check_camera(Pipe* c, const v3dg_camera* cam) {
   if (!cam) return fail(c, V3DG_EINVAL, "camera is NULL");
   if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 * 16 || cam->height > 65535 * 16)
     return fail(c, V3DG_EINVAL, "bad image size %d x %d", cam->width, cam->height);
@@ -251,10 +259,29 @@ v3dg_status setup_frame(Pipe* c, const v3dg_camera* cam, float tau_px) {
     return fail(c, V3DG_EINVAL, "bad intrinsics");
   for (double v : cam->world_to_cam)
     if (!std::isfinite(v)) return fail(c, V3DG_EINVAL, "non-finite world_to_cam");
+  return V3DG_OK;
+}
+
+// Per-frame set-up of n_views cameras (same intrinsics, image size and near plane) over the
+// pipe's instances: instance frame v * n + i holds M = W_v [s R | t] of instance i.
+v3dg_status setup_frame(Pipe* c, const v3dg_camera* cams, uint32_t n_views, float tau_px) {
+  if (!cams || n_views == 0) return fail(c, V3DG_EINVAL, "no camera");
+  for (uint32_t v = 0; v < n_views; ++v) {
+    ST(check_camera(c, cams + v));
+    const v3dg_camera& a = cams[0];
+    const v3dg_camera& b = cams[v];
+    if (b.width != a.width || b.height != a.height || b.fx != a.fx || b.fy != a.fy || b.cx != a.cx || b.cy != a.cy ||
+        b.near_z != a.near_z)
+      return fail(c, V3DG_EINVAL, "camera %u differs from camera 0 in image size, intrinsics or near plane", v);
+  }
+  const v3dg_camera* cam = cams;
   if (!(tau_px >= 0.f) || !std::isfinite(tau_px)) return fail(c, V3DG_EINVAL, "tau_px must be finite and >= 0");
   if (c->ctx->assets.empty()) return fail(c, V3DG_ENOTFOUND, "no hierarchy loaded");
   const uint64_t tiles = uint64_t((cam->width + kTile - 1) / kTile) * uint64_t((cam->height + kTile - 1) / kTile);
-  if (tiles > (1u << 24)) return fail(c, V3DG_EINVAL, "image too large (%llu tiles)", (unsigned long long)tiles);
+  if (tiles * n_views > uint64_t(kMaxTiles))
+    return fail(c, V3DG_EINVAL, "image too large (%llu tiles of 16x16 over %u views, at most %d)",
+                (unsigned long long)(tiles * n_views), n_views, kMaxTiles);
+  if (uint64_t(c->inst_asset.size()) * n_views > 0xFFFFFFFull) return fail(c, V3DG_EINVAL, "too many instance views");
   const uint32_t n = uint32_t(c->inst_asset.size());
 
   c->cam = *cam;
@@ -277,49 +304,100 @@ v3dg_status setup_frame(Pipe* c, const v3dg_camera* cam, float tau_px) {
   uint32_t max_nodes = 0;
   for (auto& a : c->ctx->assets) max_nodes = std::max(max_nodes, a.n_nodes);
   c->node_blocks = int((max_nodes + 2047) / 2048);   // k_select covers 2048 nodes per block
-  c->n_inst_frame = n;
+  c->n_inst_frame = n * n_views;
+  c->n_views = n_views;
+  // the projection is specialised for the colour formats of the assets this frame draws
+  c->color_formats = 0;
+  for (uint32_t a : c->inst_asset) c->color_formats |= c->ctx->assets[a].half_color ? 2 : 1;
+  if (!c->color_formats) c->color_formats = 1;
+  const uint32_t nf = n * n_views;
 
   // the pinned staging buffer is reused: wait until the previous upload out of it has completed
   if (c->ev_inst) CU(cudaEventSynchronize(c->ev_inst));
-  if (c->h_inst_cap < std::max<uint32_t>(n, 1)) {
+  if (c->h_inst_cap < std::max<uint32_t>(nf, 1)) {
     if (c->h_inst) cudaFreeHost(c->h_inst);
     c->h_inst = nullptr;
     c->h_inst_cap = 0;
-    CU(cudaMallocHost(&c->h_inst, sizeof(InstFrame) * std::max<uint32_t>(n, 1)));
-    c->h_inst_cap = std::max<uint32_t>(n, 1);
+    CU(cudaMallocHost(&c->h_inst, sizeof(InstFrame) * std::max<uint32_t>(nf, 1)));
+    c->h_inst_cap = std::max<uint32_t>(nf, 1);
   }
-  ST(ensure(c, c->d_inst, sizeof(InstFrame) * std::max<uint32_t>(n, 1)));
+  ST(ensure(c, c->d_inst, sizeof(InstFrame) * std::max<uint32_t>(nf, 1)));
 
-  const double* W = cam->world_to_cam;
-  double C[3];  // camera centre -R_w^T t_w
-  for (int j = 0; j < 3; ++j) C[j] = -((W[0 * 4 + j] * W[3] + W[1 * 4 + j] * W[7]) + W[2 * 4 + j] * W[11]);
-  for (uint32_t i = 0; i < n; ++i) {
-    InstFrame& f = c->h_inst[i];
-    std::memset(&f, 0, sizeof f);
-    const double* R = &c->inst_rot[9 * size_t(i)];
-    const double* t = &c->inst_trans[3 * size_t(i)];
-    const double s = c->inst_scale[i];
-    double A[9];
-    for (int q = 0; q < 9; ++q) A[q] = s * R[q];
-    for (int r = 0; r < 3; ++r) {
-      for (int col = 0; col < 3; ++col)
-        f.m64[4 * r + col] = (W[4 * r + 0] * A[0 * 3 + col] + W[4 * r + 1] * A[1 * 3 + col]) + W[4 * r + 2] * A[2 * 3 + col];
-      f.m64[4 * r + 3] = ((W[4 * r + 0] * t[0] + W[4 * r + 1] * t[1]) + W[4 * r + 2] * t[2]) + W[4 * r + 3];
+  for (uint32_t v = 0; v < n_views; ++v) {
+    const double* W = cams[v].world_to_cam;
+    double C[3];  // camera centre -R_w^T t_w
+    for (int j = 0; j < 3; ++j) C[j] = -((W[0 * 4 + j] * W[3] + W[1 * 4 + j] * W[7]) + W[2 * 4 + j] * W[11]);
+    for (uint32_t i = 0; i < n; ++i) {
+      InstFrame& f = c->h_inst[size_t(v) * n + i];
+      std::memset(&f, 0, sizeof f);
+      const double* R = &c->inst_rot[9 * size_t(i)];
+      const double* t = &c->inst_trans[3 * size_t(i)];
+      const double s = c->inst_scale[i];
+      double A[9];
+      for (int q = 0; q < 9; ++q) A[q] = s * R[q];
+      for (int r = 0; r < 3; ++r) {
+        for (int col = 0; col < 3; ++col)
+          f.m64[4 * r + col] = (W[4 * r + 0] * A[0 * 3 + col] + W[4 * r + 1] * A[1 * 3 + col]) + W[4 * r + 2] * A[2 * 3 + col];
+        f.m64[4 * r + 3] = ((W[4 * r + 0] * t[0] + W[4 * r + 1] * t[1]) + W[4 * r + 2] * t[2]) + W[4 * r + 3];
+      }
+      for (int q = 0; q < 12; ++q) f.m[q] = float(f.m64[q]);
+      for (int j = 0; j < 3; ++j) {
+        const double d = (R[0 * 3 + j] * (C[0] - t[0]) + R[1 * 3 + j] * (C[1] - t[1])) + R[2 * 3 + j] * (C[2] - t[2]);
+        f.cam_a[j] = float(d / s);
+      }
+      f.s = float(s);
+      f.s64 = s;
+      const uint32_t a = c->inst_asset[i];
+      f.asset = a;
+      f.tau_f = float(double(c->ctx->assets[a].gpg) * double(tau_px) * double(tau_px));
     }
-    for (int q = 0; q < 12; ++q) f.m[q] = float(f.m64[q]);
-    for (int j = 0; j < 3; ++j) {
-      const double d = (R[0 * 3 + j] * (C[0] - t[0]) + R[1 * 3 + j] * (C[1] - t[1])) + R[2 * 3 + j] * (C[2] - t[2]);
-      f.cam_a[j] = float(d / s);
-    }
-    f.s = float(s);
-    f.s64 = s;
-    const uint32_t a = c->inst_asset[i];
-    f.asset = a;
-    f.tau_f = float(double(c->ctx->assets[a].gpg) * double(tau_px) * double(tau_px));
   }
-  if (n) CU(cudaMemcpyAsync(c->d_inst.p, c->h_inst, sizeof(InstFrame) * n, cudaMemcpyHostToDevice, c->stream));
+  if (nf) CU(cudaMemcpyAsync(c->d_inst.p, c->h_inst, sizeof(InstFrame) * nf, cudaMemcpyHostToDevice, c->stream));
   if (!c->ev_inst) CU(cudaEventCreateWithFlags(&c->ev_inst, cudaEventDisableTiming));
   CU(cudaEventRecord(c->ev_inst, c->stream));
+  return V3DG_OK;
+}
+
+// Buffers of the top-down selection for the current instances: two frontiers that can each hold
+// every node of every instance, the per-level counts and the selection bitmap.
+v3dg_status topdown_buffers(Pipe* c, TopDown* td) {
+  uint32_t max_nodes = 0, levels = 0;
+  for (const AssetHost& a : c->ctx->assets) {
+    max_nodes = std::max(max_nodes, a.n_nodes);
+    levels = std::max(levels, a.levels);
+  }
+  const uint64_t front = std::max<uint64_t>(uint64_t(c->n_inst_frame) * max_nodes, 1);
+  if (front > 0xFFFFFFFFull) return fail(c, V3DG_EINVAL, "too many instance nodes for the top-down selection");
+  td->cap_front = uint32_t(front);
+  td->wpi = (max_nodes + 31) / 32;
+  td->steps = int(levels) + 1;   // the super-root step, then one per level
+  ST(ensure(c, c->d_front0, sizeof(uint2) * front));
+  ST(ensure(c, c->d_front1, sizeof(uint2) * front));
+  ST(ensure(c, c->d_tdcount, sizeof(uint32_t) * size_t(td->steps + 1)));
+  ST(ensure(c, c->d_bitmap, sizeof(uint32_t) * std::max<size_t>(size_t(c->n_inst_frame) * td->wpi, 1)));
+  td->frontier[0] = P<uint2>(c->d_front0);
+  td->frontier[1] = P<uint2>(c->d_front1);
+  td->counts = P<uint32_t>(c->d_tdcount);
+  td->bitmap = P<uint32_t>(c->d_bitmap);
+  return V3DG_OK;
+}
+
+// Selection into `out` (mode 0: the render list, mode 1: the cut), flat or top-down.
+v3dg_status launch_selection(Pipe* c, int mode, uint2* out, uint32_t cap, uint32_t* frame) {
+  if (!c->n_inst_frame) return V3DG_OK;
+  if (c->ctx->topdown) {
+    TopDown td{};
+    ST(topdown_buffers(c, &td));
+    int nl = 0;
+    CU(launch_select_topdown(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->ctx->d_assets), c->cc, mode,
+                             td, out, cap, frame, 0, P<uint64_t>(c->d_status), next_epoch(c), c->ctx->sm_count,
+                             c->stream, &nl));
+    c->ctx->launches += nl;
+  } else {
+    CU(launch_select(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->ctx->d_assets), c->node_blocks, c->cc,
+                     mode, out, cap, frame, 0, P<uint64_t>(c->d_status), next_epoch(c), c->stream));
+    ++c->ctx->launches;
+  }
   return V3DG_OK;
 }
 
@@ -327,12 +405,7 @@ v3dg_status enqueue_select(Pipe* c) {
   ST(ensure_work(c));
   CU(cudaMemsetAsync(c->d_frame.p, 0, sizeof(uint32_t) * kFrameWords, c->stream));
   stage_event(c, kStageSelect);
-  if (c->n_inst_frame) {
-    CU(launch_select(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->ctx->d_assets), c->node_blocks, c->cc, 0,
-                     P<uint2>(c->d_list), c->cap_nodes, P<uint32_t>(c->d_frame), 0, P<uint64_t>(c->d_status),
-                     next_epoch(c), c->stream));
-    ++c->ctx->launches;
-  }
+  ST(launch_selection(c, 0, P<uint2>(c->d_list), c->cap_nodes, P<uint32_t>(c->d_frame)));
   return V3DG_OK;
 }
 
@@ -357,7 +430,7 @@ v3dg_status enqueue_render(Pipe* c, float* rgb, float* t_out) {
                     P<float4>(c->d_ref), frame, sm, c->stream));
   CU(launch_project(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->ctx->d_assets), k,
                     P<float4>(c->d_ref), P<float4>(c->d_rec), P<uint2>(c->d_rect), P<uint32_t>(c->d_keys0), frame,
-                    color_formats(c->ctx), sm, c->stream));
+                    c->color_formats, sm, c->stream));
   c->ctx->launches += 3;
 
   stage_event(c, kStageDepthSort);
@@ -372,12 +445,14 @@ v3dg_status enqueue_render(Pipe* c, float* rgb, float* t_out) {
   const uint32_t* dslots = in1 ? P<uint32_t>(c->d_vals1) : P<uint32_t>(c->d_vals0);
 
   stage_event(c, kStageBin);
-  CU(launch_expand(dslots, P<uint2>(c->d_rect), c->cap_slots, c->cap_pairs, k.tiles_x, P<uint32_t>(c->d_pk0),
+  const int tiles_view = k.tiles_x * k.tiles_y;
+  CU(launch_expand(dslots, P<uint2>(c->d_rect), c->cap_slots, c->cap_pairs, k.tiles_x, P<uint2>(c->d_list),
+                   c->n_views > 1 ? c->n_inst_frame / c->n_views : 0u, uint32_t(tiles_view), P<uint32_t>(c->d_pk0),
                    P<uint32_t>(c->d_pv0), frame, 1, P<uint64_t>(c->d_status), next_epoch(c), c->stream));
   c->ctx->launches += 2;
 
   stage_event(c, kStageTileSort);
-  const int n_tiles = k.tiles_x * k.tiles_y;
+  const int n_tiles = tiles_view * int(c->n_views);   // (view, tile) ids
   int tile_bits = 1;
   while ((1 << tile_bits) < n_tiles) ++tile_bits;
   bool tin1 = false;
@@ -402,9 +477,9 @@ v3dg_status enqueue_render(Pipe* c, float* rgb, float* t_out) {
   unsigned long long* work = c->ctx->count_work ? reinterpret_cast<unsigned long long*>(P<uint32_t>(c->d_misc) + 8) : nullptr;
   if (work) CU(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), c->stream));
   // d_misc[12], [13]: sticky overflow / timeout flags of all frames since the last v3dg_frame_stats
-  CU(launch_blend(P<uint2>(c->d_ranges), P<uint32_t>(c->d_order), frame + kTileCounters + 10, tv, P<float4>(c->d_rec),
-                  c->cap_slots, k, rgb, t_out, work, frame, P<uint32_t>(c->d_misc) + 12, c->ctx->split_pairs, sm,
-                  c->stream));
+  CU(launch_blend(P<uint2>(c->d_ranges), P<uint32_t>(c->d_order), frame + kTileCounters + 10, tk, tv, P<float4>(c->d_rec),
+                  c->cap_slots, k, rgb, t_out, work, frame, P<uint32_t>(c->d_misc) + 12, c->ctx->split_pairs,
+                  c->ctx->blend_batch, int(c->n_views), sm, c->stream));
   c->ctx->launches += 2;
   if (work)
     CU(cudaMemcpyAsync(c->h_tmp + kFrameWords, work, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
@@ -415,6 +490,27 @@ v3dg_status enqueue_render(Pipe* c, float* rgb, float* t_out) {
 }
 
 // Runs the frame; with sync checking, waits and re-runs it with larger buffers on overflow.
+// After an overflowed frame (h_frame holds its words): grow the capacities it ran out of, clear
+// the sticky flags (the frame is re-run) and enqueue its selection again.
+v3dg_status grow_and_reselect(Pipe* c) {
+  const uint32_t* f = c->h_frame;
+  bool grew = false;
+  if (f[kRenderNodes] > c->cap_nodes) {
+    const uint64_t want = uint64_t(f[kRenderNodes]) * 5 / 4 + 1024;
+    if (want > kMaxNodes) return fail(c, V3DG_EOVERFLOW, "render list of %u nodes exceeds the limit", f[kRenderNodes]);
+    c->cap_nodes = uint32_t(want);
+    grew = true;
+  }
+  if (f[kPairs] >= c->cap_pairs || !grew) {
+    const uint64_t want = std::max<uint64_t>(uint64_t(f[kPairs]) * 5 / 4, uint64_t(c->cap_pairs) * 2);
+    if (want > kMaxPairs) return fail(c, V3DG_EOVERFLOW, "%u pairs exceed the limit", f[kPairs]);
+    c->cap_pairs = uint32_t(want);
+  }
+  CU(cudaMemsetAsync(P<uint32_t>(c->d_misc) + 12, 0, 2 * sizeof(uint32_t), c->stream));
+  ST(enqueue_select(c));
+  return V3DG_OK;
+}
+
 v3dg_status run_frame(Pipe* c, float* rgb, float* t_out, bool sync) {
   for (int attempt = 0; attempt < 8; ++attempt) {
     ST(enqueue_render(c, rgb, t_out));
@@ -423,23 +519,112 @@ v3dg_status run_frame(Pipe* c, float* rgb, float* t_out, bool sync) {
     const uint32_t* f = c->h_frame;
     if (f[kTimeout]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up; frame invalid");
     if (!f[kOverflow]) return V3DG_OK;
-    bool grew = false;
-    if (f[kRenderNodes] > c->cap_nodes) {
-      const uint64_t want = uint64_t(f[kRenderNodes]) * 5 / 4 + 1024;
-      if (want > kMaxNodes) return fail(c, V3DG_EOVERFLOW, "render list of %u nodes exceeds the limit", f[kRenderNodes]);
-      c->cap_nodes = uint32_t(want);
-      grew = true;
-    }
-    if (f[kPairs] >= c->cap_pairs || !grew) {
-      const uint64_t want = std::max<uint64_t>(uint64_t(f[kPairs]) * 5 / 4, uint64_t(c->cap_pairs) * 2);
-      if (want > kMaxPairs) return fail(c, V3DG_EOVERFLOW, "%u pairs exceed the limit", f[kPairs]);
-      c->cap_pairs = uint32_t(want);
-    }
-    // the frame is re-run: its overflow must not linger in the sticky flags
-    CU(cudaMemsetAsync(P<uint32_t>(c->d_misc) + 12, 0, 2 * sizeof(uint32_t), c->stream));
-    ST(enqueue_select(c));
+    ST(grow_and_reselect(c));
   }
   return fail(c, V3DG_EOVERFLOW, "frame still overflows after growing the buffers");
+}
+
+void drop_graph(Pipe* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->gkey.clear();
+}
+
+// What a captured frame depends on besides the contents of the instance frames (uploaded before
+// each replay): sizes, capacities, buffer addresses, camera constants, options and outputs.
+std::vector<uint64_t> graph_key(Pipe* c, float* rgb, float* t_out) {
+  const v3dg_ctx* ctx = c->ctx;
+  std::vector<uint64_t> k = {c->n_inst_frame, c->n_views, uint64_t(c->node_blocks), c->cap_nodes, c->cap_pairs,
+                             c->cap_slots, c->status_words, uint64_t(uintptr_t(rgb)), uint64_t(uintptr_t(t_out)),
+                             uint64_t(ctx->topdown), uint64_t(ctx->blend_batch), ctx->split_pairs,
+                             uint64_t(ctx->count_work), uint64_t(c->color_formats), ctx->assets.size(),
+                             uint64_t(uintptr_t(ctx->d_assets.p))};
+  const DevBuf* bufs[] = {&c->d_inst, &c->d_frame, &c->d_misc, &c->d_list, &c->d_ref, &c->d_keys0, &c->d_keys1,
+                          &c->d_vals0, &c->d_vals1, &c->d_rec, &c->d_rect, &c->d_pk0, &c->d_pk1, &c->d_pv0,
+                          &c->d_pv1, &c->d_ranges, &c->d_status, &c->d_hist, &c->d_order, &c->d_front0,
+                          &c->d_front1, &c->d_tdcount, &c->d_bitmap};
+  for (const DevBuf* b : bufs) k.push_back(uint64_t(uintptr_t(b->p)));
+  uint64_t w[sizeof(CamConst) / 8 + 1] = {};
+  std::memcpy(w, &c->cc, sizeof(CamConst));
+  for (uint64_t v : w) k.push_back(v);
+  return k;
+}
+
+// One frame as a CUDA graph: the selection and every render launch, captured on first use of a
+// configuration and replayed after that.  The chained-scan status words are cleared by the graph
+// itself, because a replay reuses the epochs that were baked in at capture.
+v3dg_status run_graph_frame(Pipe* c, float* rgb, float* t_out, bool sync) {
+  ST(ensure_work(c));
+  const int n_tiles = c->cc.tiles_x * c->cc.tiles_y * int(c->n_views);
+  ST(ensure(c, c->d_ranges, sizeof(uint2) * size_t(n_tiles)));
+  ST(ensure(c, c->d_order, sizeof(uint32_t) * (4 * size_t(n_tiles) + 1)));
+  if (c->ctx->topdown) {
+    TopDown td{};
+    ST(topdown_buffers(c, &td));
+  }
+  std::vector<uint64_t> key = graph_key(c, rgb, t_out);
+  if (!c->gexec || key != c->gkey) {
+    drop_graph(c);
+    if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CU(cudaStreamSynchronize(c->stream));   // the capture stream must not run ahead of earlier work
+    cudaStream_t saved = c->stream;
+    c->stream = c->cap_stream;
+    const uint64_t launches0 = c->ctx->launches;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    v3dg_status st = V3DG_OK;
+    if (e == cudaSuccess) {
+      e = cudaMemsetAsync(c->d_status.p, 0, sizeof(uint64_t) * size_t(c->status_words), c->cap_stream);
+      if (e == cudaSuccess) st = enqueue_select(c);
+      if (e == cudaSuccess && st == V3DG_OK) st = enqueue_render(c, rgb, t_out);
+      const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    c->stream = saved;
+    if (e == cudaSuccess && st == V3DG_OK) e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != V3DG_OK) return st;
+    if (e != cudaSuccess) {
+      c->gexec = nullptr;
+      return fail(c, V3DG_ECUDA, "frame capture failed: %s", cudaGetErrorString(e));
+    }
+    c->gkey = std::move(key);
+    c->glaunches = c->ctx->launches - launches0;
+    c->ctx->launches -= c->glaunches;   // counted when the graph runs
+  }
+  CU(cudaGraphLaunch(c->gexec, c->stream));
+  c->ctx->launches += c->glaunches;
+  c->rendered = true;
+  if (!sync) return V3DG_OK;
+  CU(cudaStreamSynchronize(c->stream));
+  if (c->h_frame[kTimeout]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up; frame invalid");
+  if (!c->h_frame[kOverflow]) return V3DG_OK;
+  ST(grow_and_reselect(c));   // grown buffers: the next frame captures a new graph
+  return run_frame(c, rgb, t_out, true);
+}
+
+// v3dg_select's launches: enqueued now, or -- for graph frames -- with the render.
+v3dg_status select_or_defer(Pipe* c) {
+  if (c->ctx->graphs && !c->ctx->stage_timing) {
+    c->select_pending = true;
+    return V3DG_OK;
+  }
+  c->select_pending = false;
+  return enqueue_select(c);
+}
+
+// The render of the current selection, as a graph or launch by launch.
+v3dg_status render_frame(Pipe* c, float* rgb, float* t_out, bool sync) {
+  const bool graph = c->ctx->graphs && !c->ctx->stage_timing;
+  if (graph) {
+    c->select_pending = false;
+    return run_graph_frame(c, rgb, t_out, sync);
+  }
+  if (c->select_pending) {
+    ST(enqueue_select(c));
+    c->select_pending = false;
+  }
+  return run_frame(c, rgb, t_out, sync);
 }
 
 v3dg_status sync_frame(Pipe* c) {
@@ -455,12 +640,7 @@ v3dg_status run_cut(Pipe* c, uint32_t* n_cut, uint32_t* n_gauss) {
   for (int attempt = 0; attempt < 8; ++attempt) {
     ST(ensure(c, c->d_cut, sizeof(uint2) * size_t(c->cap_cut)));
     CU(cudaMemsetAsync(c->d_cutframe.p, 0, sizeof(uint32_t) * kFrameWords, c->stream));
-    if (c->n_inst_frame) {
-      CU(launch_select(P<InstFrame>(c->d_inst), int(c->n_inst_frame), P<AssetDev>(c->ctx->d_assets), c->node_blocks, c->cc, 1,
-                       P<uint2>(c->d_cut), c->cap_cut, P<uint32_t>(c->d_cutframe), 0, P<uint64_t>(c->d_status),
-                       next_epoch(c), c->stream));
-      ++c->ctx->launches;
-    }
+    ST(launch_selection(c, 1, P<uint2>(c->d_cut), c->cap_cut, P<uint32_t>(c->d_cutframe)));
     CU(cudaMemcpyAsync(c->h_tmp, c->d_cutframe.p, sizeof(uint32_t) * kFrameWords, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     if (c->h_tmp[kTimeout]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up");
@@ -527,10 +707,14 @@ v3dg_status pipe_init(v3dg_ctx* ctx, Pipe* c, cudaStream_t stream) {
 
 void pipe_free(Pipe* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
   DevBuf* bs[] = {&c->d_inst, &c->d_frame, &c->d_cutframe, &c->d_misc, &c->d_list, &c->d_ref, &c->d_keys0,
                   &c->d_keys1, &c->d_vals0, &c->d_vals1, &c->d_rec, &c->d_rect, &c->d_pk0, &c->d_pk1,
                   &c->d_pv0, &c->d_pv1, &c->d_ranges, &c->d_status, &c->d_hist, &c->d_cut, &c->d_img,
-                  &c->d_timg, &c->d_sort_k, &c->d_sort_v, &c->d_order};
+                  &c->d_timg, &c->d_sort_k, &c->d_sort_v, &c->d_order, &c->d_front0, &c->d_front1,
+                  &c->d_tdcount, &c->d_bitmap};
   for (DevBuf* b : bs) dfree(c, *b);
   if (c->h_inst) cudaFreeHost(c->h_inst);
   if (c->h_frame) cudaFreeHost(c->h_frame);
@@ -569,14 +753,18 @@ struct Finished {
 
 }  // namespace
 
-// Continuous batching: each slot is a pipe with its own stream and host thread.  Requests wait in
+// Continuous batching: each slot is a pipe with its own streams and host thread.  Requests wait in
 // arrival order; a slot takes the next one as soon as it is free and the device-memory estimates
 // of the requests in flight plus this one fit the budget (one request is always admitted), so
-// requests that arrive while others run start at once and their kernels overlap on the GPU.
+// requests that arrive while others run start at once and their kernels overlap on the GPU.  A
+// request that starts while no other one is on the GPU runs on its slot's high-priority stream,
+// the others on the low-priority one: a frame that has the GPU keeps it (its latency stays that of
+// a frame alone), and the frames admitted beside it fill the SMs it leaves idle.
 struct Server {
   v3dg_ctx* ctx = nullptr;
   uint64_t budget = 0;
   std::vector<std::unique_ptr<Pipe>> slots;
+  std::vector<cudaStream_t> hi, lo;   // per slot: high- and low-priority streams
   std::vector<std::thread> threads;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -604,7 +792,7 @@ v3dg_status run_request(Pipe* c, Request& rq, Finished* f) {
   c->inst_rot.swap(rq.rot);
   c->inst_trans.swap(rq.trans);
   c->inst_scale.swap(rq.scale);
-  ST(setup_frame(c, &rq.cam, rq.tau_px));
+  ST(setup_frame(c, &rq.cam, 1, rq.tau_px));
   ST(enqueue_select(c));
   c->selected = true;
   c->rendered = false;
@@ -628,7 +816,7 @@ v3dg_status run_request(Pipe* c, Request& rq, Finished* f) {
   return V3DG_OK;
 }
 
-void slot_main(Server* sv, Pipe* p) {
+void slot_main(Server* sv, Pipe* p, size_t slot) {
   cudaSetDevice(sv->ctx->device);
   for (;;) {
     Request rq;
@@ -642,6 +830,7 @@ void slot_main(Server* sv, Pipe* p) {
       rq = std::move(sv->queue.front());
       sv->queue.pop_front();
       sv->in_flight += rq.est_bytes;
+      p->stream = sv->active == 0 ? sv->hi[slot] : sv->lo[slot];   // the previous frame of this slot has completed
       ++sv->active;
     }
     Finished f;
@@ -669,11 +858,11 @@ void server_stop(v3dg_ctx* ctx) {
   }
   sv->cv_work.notify_all();
   for (auto& t : sv->threads) t.join();
-  for (auto& p : sv->slots) {
-    cudaStream_t st = p->stream;
-    pipe_free(p.get());
+  for (auto& p : sv->slots) pipe_free(p.get());
+  for (cudaStream_t st : sv->hi)
     if (st) cudaStreamDestroy(st);
-  }
+  for (cudaStream_t st : sv->lo)
+    if (st) cudaStreamDestroy(st);
   delete sv;
   ctx->server = nullptr;
 }
@@ -702,7 +891,8 @@ v3dg_status v3dg_create(int device, const v3dg_allocator* alloc, v3dg_ctx** out)
     ctx->has_alloc = true;
   }
   if (cudaSetDevice(device) != cudaSuccess ||
-      cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      sort_set_attributes() != cudaSuccess || blend_set_attributes() != cudaSuccess) {
     delete ctx;
     return V3DG_ECUDA;
   }
@@ -723,7 +913,8 @@ void v3dg_destroy(v3dg_ctx* ctx) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   cudaDeviceSynchronize();
   for (auto& a : ctx->assets) {
-    DevBuf* bs[] = {&a.own, &a.par, &a.bound, &a.sigma, &a.flags, &a.cnt, &a.attr};
+    DevBuf* bs[] = {&a.own, &a.par, &a.bound, &a.sigma, &a.flags, &a.cnt, &a.attr, &a.child_off, &a.child_list,
+                    &a.sub_bound, &a.sub_sigma};
     for (DevBuf* b : bs) dfree(c, *b);
   }
   dfree(c, ctx->d_assets);
@@ -750,6 +941,12 @@ v3dg_status v3dg_set_option(v3dg_ctx* ctx, int option, int64_t value) {
     case V3DG_OPT_STAGE_TIMING: ctx->stage_timing = value != 0; break;
     case V3DG_OPT_COUNT_WORK: ctx->count_work = value != 0; break;
     case V3DG_OPT_ATTR_FP16: ctx->attr_fp16 = value != 0; break;
+    case V3DG_OPT_SELECT_TOPDOWN: ctx->topdown = value != 0; break;
+    case V3DG_OPT_GRAPHS: ctx->graphs = value != 0; break;
+    case V3DG_OPT_BLEND_BATCH:
+      if (value != 128 && value != 256 && value != 512) return fail(c, V3DG_EINVAL, "blend batch must be 128, 256 or 512");
+      ctx->blend_batch = int(value);
+      break;
     case V3DG_OPT_SPLIT_PAIRS:
       if (value < 1 || value > 0xFFFFFFFFll) return fail(c, V3DG_EINVAL, "split threshold out of range");
       ctx->split_pairs = uint32_t(value);
@@ -833,7 +1030,48 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* ctx, const v3dg_hierarchy_desc* d, uin
         return fail(c, V3DG_EINVAL, "non-finite Gaussian %zu", g);
     }
   }
+  // top-down traversal tables: children of every node (CSR, in node order) plus a virtual
+  // super-root (index nn) whose children are the roots; per node a sphere around the bound
+  // spheres of its whole subtree and the largest sigma in it (children before parents: by level)
+  std::vector<uint32_t> child_off(nn + 2, 0), child_list;
+  uint32_t levels = 0;
+  for (uint32_t n = 0; n < nn; ++n) {
+    const int32_t p = d->node_parent[n];
+    ++child_off[(p < 0 ? nn : uint32_t(p)) + 1];
+    levels = std::max<uint32_t>(levels, uint32_t(d->node_level[n]) + 1u);
+  }
+  for (uint32_t n = 0; n <= nn; ++n) child_off[n + 1] += child_off[n];
+  child_list.resize(child_off[nn + 1]);
+  {
+    std::vector<uint32_t> fill(child_off.begin(), child_off.end() - 1);
+    for (uint32_t n = 0; n < nn; ++n) {
+      const int32_t p = d->node_parent[n];
+      child_list[fill[p < 0 ? nn : uint32_t(p)]++] = n;
+    }
+  }
+  std::vector<float4> sub_bound(nn);
+  std::vector<float> sub_sigma(nn);
+  {
+    std::vector<uint32_t> by_level(nn);
+    for (uint32_t n = 0; n < nn; ++n) by_level[n] = n;
+    std::stable_sort(by_level.begin(), by_level.end(),
+                     [&](uint32_t x, uint32_t y) { return d->node_level[x] < d->node_level[y]; });
+    for (uint32_t n : by_level) {
+      const float4 b = bound[n];
+      double r = b.w;
+      float sg = sigma[n];
+      for (uint32_t q = child_off[n]; q < child_off[n + 1]; ++q) {
+        const float4 cb = sub_bound[child_list[q]];
+        const double dx = double(cb.x) - b.x, dy = double(cb.y) - b.y, dz = double(cb.z) - b.z;
+        r = std::max(r, std::sqrt(dx * dx + dy * dy + dz * dz) + double(cb.w));
+        sg = std::max(sg, sub_sigma[child_list[q]]);
+      }
+      sub_bound[n] = make_float4(b.x, b.y, b.z, round_up_f(r * (1.0 + 1e-6)));
+      sub_sigma[n] = sg;
+    }
+  }
   AssetHost a;
+  a.levels = levels;
   a.n_gauss = d->n_gauss;
   a.n_nodes = nn;
   a.sh_coeffs = coeffs;
@@ -850,8 +1088,13 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* ctx, const v3dg_hierarchy_desc* d, uin
       (s = up(a.bound, bound.data(), sizeof(float4) * nn)) != V3DG_OK ||
       (s = up(a.sigma, sigma.data(), sizeof(float) * nn)) != V3DG_OK ||
       (s = up(a.flags, flags.data(), nn)) != V3DG_OK || (s = up(a.cnt, cnt.data(), nn)) != V3DG_OK ||
-      (s = up(a.attr, attr.data(), attr.size())) != V3DG_OK) {
-    DevBuf* bs[] = {&a.own, &a.par, &a.bound, &a.sigma, &a.flags, &a.cnt, &a.attr};
+      (s = up(a.attr, attr.data(), attr.size())) != V3DG_OK ||
+      (s = up(a.child_off, child_off.data(), sizeof(uint32_t) * child_off.size())) != V3DG_OK ||
+      (s = up(a.child_list, child_list.data(), sizeof(uint32_t) * std::max<size_t>(child_list.size(), 1))) != V3DG_OK ||
+      (s = up(a.sub_bound, sub_bound.data(), sizeof(float4) * nn)) != V3DG_OK ||
+      (s = up(a.sub_sigma, sub_sigma.data(), sizeof(float) * nn)) != V3DG_OK) {
+    DevBuf* bs[] = {&a.own, &a.par, &a.bound, &a.sigma, &a.flags, &a.cnt, &a.attr, &a.child_off, &a.child_list,
+                    &a.sub_bound, &a.sub_sigma};
     for (DevBuf* b : bs) dfree(c, *b);
     return s;
   }
@@ -871,6 +1114,11 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* ctx, const v3dg_hierarchy_desc* d, uin
     t.stride = uint32_t(cluster_block_bytes(int(h.sh_coeffs), h.half_color));
     t.sh_coeffs = h.sh_coeffs;
     t.half_color = h.half_color ? 1u : 0u;
+    t.child_off = P<uint32_t>(h.child_off);
+    t.child_list = P<uint32_t>(h.child_list);
+    t.sub_bound = P<float4>(h.sub_bound);
+    t.sub_sigma = P<float>(h.sub_sigma);
+    t.root = h.n_nodes;
   }
   ST(ensure(c, ctx->d_assets, sizeof(AssetDev) * table.size()));
   CU(cudaMemcpy(ctx->d_assets.p, table.data(), sizeof(AssetDev) * table.size(), cudaMemcpyHostToDevice));
@@ -905,8 +1153,20 @@ v3dg_status v3dg_select(v3dg_ctx* ctx, const v3dg_camera* cam, float tau_px) {
   Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
   CU(cudaSetDevice(ctx->device));
-  ST(setup_frame(c, cam, tau_px));
-  ST(enqueue_select(c));
+  ST(setup_frame(c, cam, 1, tau_px));
+  ST(select_or_defer(c));
+  c->selected = true;
+  c->rendered = false;
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_select_views(v3dg_ctx* ctx, const v3dg_camera* cams, uint32_t n_views, float tau_px) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
+  if (!c) return V3DG_EINVAL;
+  CU(cudaSetDevice(ctx->device));
+  ST(setup_frame(c, cams, n_views, tau_px));
+  ST(select_or_defer(c));
   c->selected = true;
   c->rendered = false;
   c->err.clear();
@@ -918,7 +1178,7 @@ v3dg_status v3dg_render(v3dg_ctx* ctx, float* rgb_out, float* t_out) {
   if (!c) return V3DG_EINVAL;
   if (!c->selected) return fail(c, V3DG_ENOTFOUND, "v3dg_render without a prior v3dg_select");
   if (!rgb_out) return fail(c, V3DG_EINVAL, "rgb_out is NULL");
-  ST(run_frame(c, rgb_out, t_out, ctx->sync_check));
+  ST(render_frame(c, rgb_out, t_out, ctx->sync_check));
   c->err.clear();
   return V3DG_OK;
 }
@@ -928,10 +1188,10 @@ v3dg_status v3dg_render_host(v3dg_ctx* ctx, float* rgb_host, float* t_host) {
   if (!c) return V3DG_EINVAL;
   if (!c->selected) return fail(c, V3DG_ENOTFOUND, "v3dg_render_host without a prior v3dg_select");
   if (!rgb_host) return fail(c, V3DG_EINVAL, "rgb_host is NULL");
-  const size_t px = size_t(c->cam.width) * size_t(c->cam.height);
+  const size_t px = size_t(c->cam.width) * size_t(c->cam.height) * c->n_views;
   ST(ensure(c, c->d_img, sizeof(float) * 3 * px));
   if (t_host) ST(ensure(c, c->d_timg, sizeof(float) * px));
-  ST(run_frame(c, P<float>(c->d_img), t_host ? P<float>(c->d_timg) : nullptr, ctx->sync_check));
+  ST(render_frame(c, P<float>(c->d_img), t_host ? P<float>(c->d_timg) : nullptr, ctx->sync_check));
   CU(cudaMemcpyAsync(rgb_host, c->d_img.p, sizeof(float) * 3 * px, cudaMemcpyDeviceToHost, c->stream));
   if (t_host) CU(cudaMemcpyAsync(t_host, c->d_timg.p, sizeof(float) * px, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -945,6 +1205,10 @@ v3dg_status v3dg_frame_stats(v3dg_ctx* ctx, v3dg_stats* out) {
   Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c || !out) return V3DG_EINVAL;
   if (!c->selected) return fail(c, V3DG_ENOTFOUND, "no frame selected");
+  if (c->select_pending) {   // a graph frame's selection not rendered yet: run it now for the counters
+    ST(enqueue_select(c));
+    c->select_pending = false;
+  }
   ST(sync_frame(c));
   std::memset(out, 0, sizeof *out);
   const uint32_t* f = c->h_frame;
@@ -1017,7 +1281,7 @@ v3dg_status v3dg_get_projected(v3dg_ctx* ctx, uint64_t cap, uint64_t* n, uint32_
     std::memcpy(&org, &r2.y, 4);
     const uint2 rr = rc[slot];
     if (inst) inst[q] = e.x;
-    if (local) local[q] = ctx->assets[c->inst_asset[e.x]].node_first[e.y] + j;
+    if (local) local[q] = ctx->assets[c->inst_asset[e.x % c->inst_asset.size()]].node_first[e.y] + j;
     if (u) {
       u[2 * q] = float(double(r0.x) + 16.0 * double(org & 0xFFFFu));
       u[2 * q + 1] = float(double(r0.y) + 16.0 * double(org >> 16));
@@ -1035,10 +1299,10 @@ v3dg_status v3dg_get_projected(v3dg_ctx* ctx, uint64_t cap, uint64_t* n, uint32_
     }
     if (depth_key) depth_key[q] = keys[k];
     if (rect) {
-      rect[4 * q] = int32_t(rr.x & 0xFFFFu);
-      rect[4 * q + 1] = int32_t(rr.x >> 16);
-      rect[4 * q + 2] = int32_t(rr.y & 0xFFFFu);
-      rect[4 * q + 3] = int32_t(rr.y >> 16);
+      rect[4 * q] = int32_t((rr.x & 0xFFFFu) >> 4);   // the pixel box's tiles
+      rect[4 * q + 1] = int32_t((rr.x >> 16) >> 4);
+      rect[4 * q + 2] = int32_t((rr.y & 0xFFFFu) >> 4);
+      rect[4 * q + 3] = int32_t((rr.y >> 16) >> 4);
     }
   }
   c->err.clear();
@@ -1071,13 +1335,13 @@ v3dg_status v3dg_get_pairs(v3dg_ctx* ctx, uint64_t cap, uint64_t* n, uint32_t* t
     if (slots[k] < key_of.size()) key_of[slots[k]] = keys[k];
   for (uint64_t q = 0; q < m; ++q) {
     const uint32_t slot = tv[q];
-    if (tile) tile[q] = tk[q];
+    if (tile) tile[q] = tk[q] & kPairTileMask;
     if (slot / kSlots >= nr) return fail(c, V3DG_EINVAL, "pair %llu references slot %u beyond the render list",
                                          (unsigned long long)q, slot);
     const uint2 e = list[slot / kSlots];
     if (depth_key) depth_key[q] = key_of[slot];
     if (inst) inst[q] = e.x;
-    if (local) local[q] = ctx->assets[c->inst_asset[e.x]].node_first[e.y] + slot % kSlots;
+    if (local) local[q] = ctx->assets[c->inst_asset[e.x % c->inst_asset.size()]].node_first[e.y] + slot % kSlots;
   }
   c->err.clear();
   return V3DG_OK;
@@ -1088,7 +1352,7 @@ v3dg_status v3dg_get_tile_ranges(v3dg_ctx* ctx, uint32_t* range, uint64_t cap, u
   if (!c || !n_tiles) return V3DG_EINVAL;
   if (!c->rendered) return fail(c, V3DG_ENOTFOUND, "no frame rendered");
   ST(sync_frame(c));
-  const uint64_t nt = uint64_t(c->cc.tiles_x) * uint64_t(c->cc.tiles_y);
+  const uint64_t nt = uint64_t(c->cc.tiles_x) * uint64_t(c->cc.tiles_y) * c->n_views;
   *n_tiles = nt;
   if (range && cap) CU(cudaMemcpy(range, c->d_ranges.p, sizeof(uint2) * std::min(cap, nt), cudaMemcpyDeviceToHost));
   c->err.clear();
@@ -1104,6 +1368,66 @@ v3dg_status v3dg_stage_times(v3dg_ctx* ctx, float* ms, int n, uint64_t* launches
     CU(cudaStreamSynchronize(c->stream));
     for (int i = 0; i < n && i < kStages; ++i) CU(cudaEventElapsedTime(ms + i, c->ev[i], c->ev[i + 1]));
   }
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* batch_out, uint32_t* split_out, float* ms_out) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
+  if (!c) return V3DG_EINVAL;
+  if (!c->rendered) return fail(c, V3DG_ENOTFOUND, "no frame rendered");
+  ST(sync_frame(c));
+  if (c->h_frame[kOverflow] || c->h_frame[kTimeout]) return fail(c, V3DG_EOVERFLOW, "the last frame was not valid");
+  const CamConst& k = c->cc;
+  const size_t px = size_t(k.width) * size_t(k.height) * c->n_views;
+  ST(ensure(c, c->d_img, sizeof(float) * 3 * std::max<size_t>(px, 1)));
+  const uint32_t* tk = P<uint32_t>(c->tiles_in1 ? c->d_pk1 : c->d_pk0);
+  const uint32_t* tv = P<uint32_t>(c->tiles_in1 ? c->d_pv1 : c->d_pv0);
+  uint32_t* frame = P<uint32_t>(c->d_frame);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, V3DG_ECUDA, "cudaEventCreate failed");
+  }
+  const int batches[] = {128, 256, 512};
+  const uint32_t splits[] = {4096u, 16384u, 65536u, 0xFFFFFFFFu};
+  float best = INFINITY;
+  int best_b = ctx->blend_batch;
+  uint32_t best_s = ctx->split_pairs;
+  cudaError_t e = cudaSuccess;
+  for (int b : batches) {
+    for (uint32_t sp : splits) {
+      float t_min = INFINITY;
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // the first run warms up
+        e = cudaMemsetAsync(frame + kTileCounters + 10, 0, sizeof(uint32_t), c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess)
+          e = launch_blend(P<uint2>(c->d_ranges), P<uint32_t>(c->d_order), frame + kTileCounters + 10, tk, tv,
+                           P<float4>(c->d_rec), c->cap_slots, k, P<float>(c->d_img), nullptr, nullptr, frame,
+                           P<uint32_t>(c->d_misc) + 12, sp, b, int(c->n_views), ctx->sm_count, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0) t_min = std::min(t_min, ms);
+        ctx->launches += 2;
+      }
+      if (t_min < best) {
+        best = t_min;
+        best_b = b;
+        best_s = sp;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(c, V3DG_ECUDA, "CUDA error %s", cudaGetErrorString(e));
+  ctx->blend_batch = best_b;
+  ctx->split_pairs = best_s;
+  if (batch_out) *batch_out = uint32_t(best_b);
+  if (split_out) *split_out = best_s;
+  if (ms_out) *ms_out = best;
   c->err.clear();
   return V3DG_OK;
 }
@@ -1152,16 +1476,22 @@ v3dg_status v3dg_server_start(v3dg_ctx* ctx, int slots, uint64_t hbm_budget) {
   if (!sv) return fail(c, V3DG_ENOMEM, "out of host memory");
   sv->ctx = ctx;
   sv->budget = hbm_budget ? hbm_budget : ~uint64_t(0);
+  int least = 0, greatest = 0;
+  CU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
   for (int i = 0; i < slots; ++i) {
     auto p = std::make_unique<Pipe>();
     p->ctx_alloc = false;   // workers use cudaMalloc: the allocator is called from the owner's thread only
-    cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStream_t hi = nullptr, lo = nullptr;
+    const bool ok = cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+                    cudaStreamCreateWithPriority(&lo, cudaStreamNonBlocking, least) == cudaSuccess;
+    sv->hi.push_back(hi);
+    sv->lo.push_back(lo);
+    if (!ok) {
       ctx->server = sv;
       server_stop(ctx);
-      return fail(c, V3DG_ECUDA, "cudaStreamCreate failed");
+      return fail(c, V3DG_ECUDA, "cudaStreamCreateWithPriority failed");
     }
-    const v3dg_status s = pipe_init(ctx, p.get(), st);
+    const v3dg_status s = pipe_init(ctx, p.get(), hi);
     sv->slots.push_back(std::move(p));
     if (s != V3DG_OK) {
       ctx->server = sv;
@@ -1170,7 +1500,7 @@ v3dg_status v3dg_server_start(v3dg_ctx* ctx, int slots, uint64_t hbm_budget) {
     }
   }
   ctx->server = sv;
-  for (auto& p : sv->slots) sv->threads.emplace_back(slot_main, sv, p.get());
+  for (size_t i = 0; i < sv->slots.size(); ++i) sv->threads.emplace_back(slot_main, sv, sv->slots[i].get(), i);
   c->err.clear();
   return V3DG_OK;
 }
@@ -1190,6 +1520,8 @@ v3dg_status v3dg_submit(v3dg_ctx* ctx, const v3dg_request* req, uint64_t* ticket
   if (!req->rgb_out) return V3DG_EINVAL;
   const v3dg_camera& cam = req->camera;
   if (cam.width <= 0 || cam.height <= 0 || !(cam.fx > 0.f) || !(cam.fy > 0.f) || !(req->tau_px >= 0.f))
+    return V3DG_EINVAL;
+  if (uint64_t((cam.width + kTile - 1) / kTile) * uint64_t((cam.height + kTile - 1) / kTile) > uint64_t(kMaxTiles))
     return V3DG_EINVAL;
   for (uint32_t i = 0; i < n; ++i) {
     if (req->asset_id[i] >= ctx->assets.size()) return V3DG_ENOTFOUND;

@@ -149,21 +149,38 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
                         const SortScratch& sc, uint32_t* err_flag, uint32_t& epoch, int sm_count,
                         cudaStream_t st, bool* result_in_1, int* launches);
 
+// Pair keys: tile id in bits 0..19 (at most 2^20 tiles), then the Gaussian's pixel box clipped
+// to the tile, tile-local and inclusive: rows y0 in bits 20..23 and y1 in 24..27, columns rounded
+// out to quads of 4, x0 / 4 in bits 28..29 and x1 / 4 in 30..31.
+constexpr uint32_t kPairTileMask = 0xFFFFFu;
+constexpr int kMaxTiles = 1 << 20;
+
+// Per-device kernel attributes (shared-memory carveouts), set once per context before any launch
+// (so that no attribute call happens during a stream capture).
+cudaError_t sort_set_attributes();
+cudaError_t blend_set_attributes();
+
 // Expansion of the depth-sorted visible Gaussians into (tile, slot) pairs in depth order; writes
-// frame[kPairs] (the total) and frame[kPairsEff] (0 if the frame overflowed).
+// frame[kPairs] (the total) and frame[kPairsEff] (0 if the frame overflowed).  rect: per slot,
+// the pixel box (x0 | x1 << 16, y0 | y1 << 16) of the alpha >= 1/255 ellipse, inclusive.
+// Several views: the render list's instance frames are view * inst_per_view + instance, and the
+// tile id of a pair is view * tiles_per_view + tile (inst_per_view 0: one view, list unused).
 cudaError_t launch_expand(const uint32_t* sorted_slots, const uint2* rect, uint32_t cap_slots, uint32_t cap_pairs,
-                          int tiles_x, uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* frame,
-                          uint32_t tile_counter_slot, uint64_t* status, uint32_t epoch, cudaStream_t st);
+                          int tiles_x, const uint2* list, uint32_t inst_per_view, uint32_t tiles_per_view,
+                          uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* frame, uint32_t tile_counter_slot,
+                          uint64_t* status, uint32_t epoch, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const uint32_t* frame,
                           uint2* ranges, int n_tiles, int sm_count, cudaStream_t st);
 // work != nullptr: also count (evaluations, contributions) into work[0], work[1].
 // sticky[0] |= frame[kOverflow], sticky[1] |= frame[kTimeout] (the flags of every frame since the
 // host last cleared them).
 // items: 4 * n_tiles + 1 words of scratch (the heaviest-first work items and their count);
-// tile_counter: a zeroed word.
-cudaError_t launch_blend(const uint2* ranges, uint32_t* items, uint32_t* tile_counter, const uint32_t* pair_vals,
-                         const float4* rec, uint32_t cap_slots, const CamConst& cam, float* rgb, float* t_out,
+// tile_counter: a zeroed word.  batch: records staged per batch, 128, 256 or 512.  n_views
+// images of cam's size, one after the other in rgb (and t_out); tile ids are (view, tile).
+// tk, pair_vals: the sorted pair keys (tile id and in-tile box, see kPairTileMask) and values.
+cudaError_t launch_blend(const uint2* ranges, uint32_t* items, uint32_t* tile_counter, const uint32_t* tk,
+                         const uint32_t* pair_vals, const float4* rec, uint32_t cap_slots, const CamConst& cam, float* rgb, float* t_out,
                          unsigned long long* work, const uint32_t* frame, uint32_t* sticky, uint32_t split_pairs,
-                         int sm_count, cudaStream_t st);
+                         int batch, int n_views, int sm_count, cudaStream_t st);
 
 }  // namespace v3dg

@@ -224,3 +224,109 @@ def test_fp16_attributes_parity(Context, tiny_asset, view):
     p32 = oracle.project([tiny_asset], inst, cam, cut)
     C32, _, _ = oracle.render_image(p32, cam.width, cam.height)
     assert oracle.psnr(out["rgb"], C32) >= PSNR_MIN
+
+
+@pytest.mark.parametrize("view,tau", [(0, 0.5), (1, 0.5), (1, 1.0), (2, 2.0)])
+def test_paper_shaped_bundle(Context, view, tau):
+    """The paper's bundle shape (4096-Gaussian clusters, binary tree, halving simplification,
+    tau in the paper's units: tau_px = 0.5 is tau_F = 2048 px^2): cut, records, pairs and image."""
+    from synth.paper_tree import make_asset_paper
+    asset = make_asset_paper(0, 100_000)
+    cam = [scenes.tiny_camera(), scenes.orbit_camera(4.0, 320, 180), scenes.orbit_camera(12.0, 320, 180)][view]
+    inst = scenes.single_instance()
+    out = _frame(Context, [asset], inst, cam, tau)
+    cut = oracle.select([asset], inst, cam, tau)
+    assert_cut_parity(out["cut"], cut)
+    p = oracle.project([asset], inst, cam, cut)
+    assert_projection_parity(out["proj"], p)
+    assert_pairs_parity(out["pairs"], p, cam)
+    C, T, B = oracle.render_image(p, cam.width, cam.height)
+    err, ps, nb = image_errors(out["rgb"], C, B)
+    assert err <= IMG_ABS and ps >= PSNR_MIN, (err, ps)
+
+
+def test_blend_batch_sizes_and_autotuner(Context, tiny_asset, small_asset):
+    """Every blend batch size gives the same image bit for bit; the autotuner needs a rendered
+    frame, picks one of its candidates, keeps it, and the frames after it are unchanged."""
+    from paper_2505_06523_gb300._native import V3DG_OPT_BLEND_BATCH, V3dgError
+    inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+    cam = scenes.crowd_camera(40, 640, 360)
+    outs = [_frame(Context, [tiny_asset, small_asset], inst, cam, 1.0, {V3DG_OPT_BLEND_BATCH: b}) for b in (128, 256, 512)]
+    assert float(np.abs(outs[0]["rgb"]).sum()) > 0
+    for o in outs[1:]:
+        assert (o["rgb"] == outs[0]["rgb"]).all() and (o["T"] == outs[0]["T"]).all()
+    with Context(0) as ctx:
+        for a in (tiny_asset, small_asset):
+            ctx.load_hierarchy(a)
+        ctx.set_instances(inst)
+        with pytest.raises(V3dgError):
+            ctx.autotune_blend()
+        ctx.select(cam, 1.0)
+        ctx.render()
+        r = ctx.autotune_blend()
+        assert r["batch"] in (128, 256, 512) and r["split_pairs"] in (4096, 16384, 65536, 0xFFFFFFFF) and r["ms"] > 0
+        ctx.select(cam, 1.0)
+        rgb, T = ctx.render(want_T=True)
+        assert (rgb.cpu().numpy() == outs[0]["rgb"]).all() and (T.cpu().numpy() == outs[0]["T"]).all()
+
+
+def test_views_batch_equals_single_views(Context, tiny_asset, small_asset):
+    """Several cameras in one batch: every stage runs once for all views, and each view's image,
+    cut and counters are those of the view rendered alone, bit for bit."""
+    inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+    assets = [tiny_asset, small_asset]
+    cams = [scenes.crowd_camera(t, 480, 270) for t in (0, 40, 150, 151)]
+    singles = [_frame(Context, assets, inst, cam, 1.0) for cam in cams]
+    with Context(0) as ctx:
+        for a in assets:
+            ctx.load_hierarchy(a)
+        ctx.set_instances(inst)
+        ctx.select_views(cams, 1.0)
+        rgb, T = ctx.render(want_T=True)
+        cut = ctx.get_cut()
+        ranges = ctx.tile_ranges()
+        host_rgb, host_T = ctx.render_host(want_T=True)
+    rgb, T = rgb.cpu().numpy(), T.cpu().numpy()
+    assert rgb.shape == (4, 270, 480, 3) and ranges.shape[0] == 4 * 30 * 17
+    n = inst.n
+    for v, one in enumerate(singles):
+        assert (rgb[v] == one["rgb"]).all() and (T[v] == one["T"]).all(), v
+        assert (host_rgb[v] == one["rgb"]).all() and (host_T[v] == one["T"]).all(), v
+        mine = cut[(cut[:, 0] >= v * n) & (cut[:, 0] < (v + 1) * n)].copy()
+        mine[:, 0] -= v * n
+        assert np.array_equal(mine, one["cut"])
+        rv = ranges[v * 510:(v + 1) * 510].astype(np.int64)
+        assert ((rv[:, 1] - rv[:, 0]) == (one["ranges"][:, 1].astype(np.int64) - one["ranges"][:, 0])).all()
+    with pytest.raises(Exception):
+        with Context(0) as ctx:
+            ctx.load_hierarchy(tiny_asset)
+            ctx.set_instances(inst)
+            ctx.select_views([cams[0], scenes.crowd_camera(3, 320, 180)], 1.0)
+
+
+def test_graph_frames_match_launch_by_launch(Context, tiny_asset, small_asset):
+    """CUDA-graph frames: the same images as launching stage by stage, through a buffer overflow
+    (the frame is re-run and grows), a camera walk that reuses the captured graph, and an image
+    size change that captures a new one."""
+    from paper_2505_06523_gb300._native import V3DG_OPT_CAP_NODES, V3DG_OPT_CAP_PAIRS, V3DG_OPT_GRAPHS
+    inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+    cams = [scenes.crowd_camera(t, 320, 180) for t in (0, 13, 26, 39)] + [scenes.crowd_camera(50, 480, 270)]
+    out = {}
+    for graphs in (0, 1):
+        imgs = []
+        with Context(0) as ctx:
+            ctx.set_option(V3DG_OPT_GRAPHS, graphs)
+            ctx.set_option(V3DG_OPT_CAP_NODES, 64)
+            ctx.set_option(V3DG_OPT_CAP_PAIRS, 4096)
+            for a in (tiny_asset, small_asset):
+                ctx.load_hierarchy(a)
+            ctx.set_instances(inst)
+            for cam in cams + cams[:2]:
+                ctx.select(cam, 1.0)
+                rgb, T = ctx.render(want_T=True)
+                st = ctx.frame_stats()
+                imgs.append((rgb.cpu().numpy(), T.cpu().numpy(), st["pairs"], st["render_nodes"]))
+        out[graphs] = imgs
+    assert float(np.abs(out[0][0][0]).sum()) > 0
+    for (r0, t0, p0, n0), (r1, t1, p1, n1) in zip(out[0], out[1]):
+        assert (r0 == r1).all() and (t0 == t1).all() and p0 == p1 and n0 == n1

@@ -347,3 +347,14 @@ def test_nodes_reaching_pixels_keeps_every_contributor(small_asset):
     c0, t0, b0 = oracle.render_pixels(p, pix)
     c1, t1, b1 = oracle.render_pixels(ps, pix)
     assert np.array_equal(c0, c1) and np.array_equal(t0, t1) and np.array_equal(b0, b1)
+    # the Gaussian-level bound on top of it keeps every contributor too, and far fewer Gaussians
+    sub2, only = oracle.gaussians_reaching_pixels([small_asset], inst, cam, cut, pix)
+    pg = oracle.project([small_asset], inst, cam, sub2, only=only)
+    kept_g = set((pg.inst.astype(np.int64) << 32 | pg.local.astype(np.int64)).tolist())
+    assert kept_g <= kept
+    for px, py in pix:
+        al = oracle.gaussian_alpha(p, vis, px, py)
+        hit = vis[al >= oracle.ALPHA_MIN]
+        assert kept_g.issuperset((p.inst[hit].astype(np.int64) << 32 | p.local[hit].astype(np.int64)).tolist())
+    c2, t2, b2 = oracle.render_pixels(pg, pix)
+    assert np.array_equal(c0, c2) and np.array_equal(t0, t2) and np.array_equal(b0, b2)
