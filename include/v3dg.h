@@ -112,8 +112,8 @@ enum {
   V3DG_OPT_CAP_PAIRS = 4,    /* current (tile, Gaussian) pair capacity (>= 4096); grows on demand */
   V3DG_OPT_COUNT_WORK = 5,   /* 1: the blend also counts its evaluations (v3dg_stats.blend_*) */
   V3DG_OPT_SPLIT_PAIRS = 6,  /* tiles with at least this many pairs are blended as four 8x8
-                                quadrants by separate blocks (default 16384; the image does not
-                                depend on it) */
+                                quadrants by separate blocks (default 2^32 - 1: no split; the
+                                image does not depend on it) */
   V3DG_OPT_ATTR_FP16 = 7,    /* 1: assets loaded from now on keep opacity and SH in float16 (rounded
                                 to nearest even); means, scales and rotations stay float32 and all
                                 arithmetic stays float32 */

@@ -236,8 +236,9 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
             const uint32_t stop = min(e1, ee);
             const float4 g = s_g[j], c = s_c[j];
             const uint32_t bit = 1u << (j & 31);
+            uint32_t row = s_live[yy >> 1] >> ((yy & 1) * 16);   // live pixels of row yy
             for (; e < stop; ++e) {
-              if ((s_live[yy >> 1] >> ((yy & 1) * 16 + xx)) & 1u) {   // pixel still accumulating
+              if ((row >> xx) & 1u) {   // pixel still accumulating
                 const float l2a = log2_alpha(g, c, float(xx) + 0.5f, float(yy) + 0.5f);
                 if (kCount) ++n_eval;
                 if (l2a >= kLog2MinAlpha && fminf(0.999f, exp2f(l2a)) >= 1.f / 255.f)
@@ -246,6 +247,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
               if (++xx > x1) {
                 xx = x0;
                 ++yy;
+                row = yy < 16 ? s_live[yy >> 1] >> ((yy & 1) * 16) : 0u;
               }
             }
             ++j;
@@ -260,23 +262,45 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
         if (!bits) continue;
         s_mask[threadIdx.x][wd] = 0u;
         while (bits && !done) {
-          const int j = wd * 32 + __ffs(bits) - 1;
-          bits &= bits - 1;
-          const float4 c = s_c[j];
-          const float l2a = log2_alpha(s_g[j], c, fx, fy);
-          const float alpha = fminf(0.999f, exp2f(l2a));
-          if (l2a < kLog2MinAlpha || alpha < 1.f / 255.f) continue;
-          const float tn = T * (1.f - alpha);
-          if (tn < 1e-4f) {
-            done = true;
-            break;
+          // two records at a time: their alphas are independent, only T is a chain
+          constexpr int kAhead = 2;
+          int jj[kAhead], n = 0;
+#pragma unroll
+          for (int q = 0; q < kAhead; ++q) {
+            jj[q] = wd * 32 + __ffs(bits) - 1;   // bits == 0: a valid index, not used
+            if (bits) {
+              bits &= bits - 1;
+              n = q + 1;
+            }
           }
-          if (kCount) ++n_contrib;
-          const float wgt = alpha * T;
-          cr = fmaf(wgt, c.z, cr);
-          cg = fmaf(wgt, c.w, cg);
-          cb = fmaf(wgt, s_b[j], cb);
-          T = tn;
+          float a[kAhead], r[kAhead], g[kAhead], b[kAhead];
+#pragma unroll
+          for (int q = 0; q < kAhead; ++q) {
+            const int j = max(jj[q], wd * 32);
+            const float4 c = s_c[j];
+            const float l2a = log2_alpha(s_g[j], c, fx, fy);
+            // alpha < 1/255 (also when log2 alpha is below the threshold) is skipped below
+            a[q] = l2a < kLog2MinAlpha ? 0.f : fminf(0.999f, exp2f(l2a));
+            r[q] = c.z;
+            g[q] = c.w;
+            b[q] = s_b[j];
+          }
+#pragma unroll
+          for (int q = 0; q < kAhead; ++q) {
+            if (q >= n || done) break;
+            if (a[q] < 1.f / 255.f) continue;
+            const float tn = T * (1.f - a[q]);
+            if (tn < 1e-4f) {
+              done = true;
+              break;
+            }
+            if (kCount) ++n_contrib;
+            const float wgt = a[q] * T;
+            cr = fmaf(wgt, r[q], cr);
+            cg = fmaf(wgt, g[q], cg);
+            cb = fmaf(wgt, b[q], cb);
+            T = tn;
+          }
         }
       }
       __syncthreads();

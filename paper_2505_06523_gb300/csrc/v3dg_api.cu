@@ -113,7 +113,7 @@ struct v3dg_ctx {
   DevBuf d_assets;
   std::atomic<uint64_t> launches{0};
   bool sync_check = true, stage_timing = false, count_work = false;
-  uint32_t split_pairs = 16384;
+  uint32_t split_pairs = 0xFFFFFFFFu;   // long-tile split threshold (none by default)
   bool attr_fp16 = false;   // store opacity and SH of the next loaded assets as float16
   bool topdown = false;     // select level by level from the roots (same cut as the flat kernel)
   int blend_batch = 256;    // records staged per blend batch: 128, 256 or 512
