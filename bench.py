@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--assets", type=int, default=N_ASSETS, help="fewer assets: a smaller case for profiling")
     ap.add_argument("--instances", type=int, default=N_INST, help="fewer instances: a smaller case for profiling")
     ap.add_argument("--slots", type=int, default=4, help="server slots of the served leg (0: no served leg)")
-    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-requests", type=int, default=150)
+    ap.add_argument("--views", type=int, default=8, help="views per launch of the batched leg (0: none)")
     return ap.parse_args()
 
 
@@ -328,6 +329,8 @@ def main():
                            {"batch": tuned["batch"], "split_pairs": tuned["split_pairs"]})
         served["autotune"] = tuned
         served["psnr_fp16_vs_fp32_db"] = fp16_psnr(ctx, inst, inst16, cams, timed_ids, args.tau)
+        if args.views > 0:
+            served["batched"] = batched_leg(ctx, inst, inst16, cams, timed_ids, args.tau, args.views, tuned)
 
     peaks, peak_kind = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
@@ -416,7 +419,7 @@ def _pcts(lat):
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
 
 
-DEFAULT_BLEND = {"batch": 256, "split_pairs": 16384}
+DEFAULT_BLEND = {"batch": 256, "split_pairs": 0xFFFFFFFF}
 
 
 def _blend_options(ctx, opts):
@@ -466,6 +469,58 @@ def serve_leg(ctx, inst, inst16, cams, frame_ids, tau, slots, n_req, tuned):
         "frames_per_s": cap["served"] / cap["plain"],
         "p99_at_90pct_load": out["served"]["poisson"][1]["p99_ms"] / out["plain"]["poisson"][1]["p99_ms"]}
     return out
+
+
+def batched_leg(ctx, inst, inst16, cams, frame_ids, tau, views, tuned):
+    """Frames in batches: `views` consecutive walk frames per v3dg_select_views + v3dg_render
+    (every stage one launch for all of them), replayed as a CUDA graph, FP16 colour, autotuned
+    blend; device images.  frames/s = views x batches / time (CUDA events), beside the same frames
+    one at a time with the same options."""
+    import torch
+    from paper_2505_06523_gb300 import _native as N
+    _blend_options(ctx, tuned)
+    ctx.set_instances(inst16)
+    ctx.set_option(N.V3DG_OPT_GRAPHS, 1)
+    groups = [[cams[(f + v) % len(cams)] for v in range(views)] for f in frame_ids[:6]]
+    out = torch.empty((views, HEIGHT, WIDTH, 3), dtype=torch.float32, device="cuda")
+    for g in groups[:2]:   # buffers grow, the graph is captured
+        ctx.select_views(g, tau)
+        ctx.render(out)
+    ctx.set_option(N.V3DG_OPT_SYNC_CHECK, 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    for g in groups:
+        ctx.select_views(g, tau)
+        ctx.render(out)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1)
+    st = ctx.frame_stats()
+    one = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32, device="cuda")
+    for g in groups[:1]:
+        for cam in g:
+            ctx.select(cam, tau)
+            ctx.render(one)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    for g in groups:
+        for cam in g:
+            ctx.select(cam, tau)
+            ctx.render(one)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1)
+    ctx.set_option(N.V3DG_OPT_SYNC_CHECK, 1)
+    ctx.set_option(N.V3DG_OPT_GRAPHS, 0)
+    ctx.set_instances(inst)
+    _blend_options(ctx, DEFAULT_BLEND)
+    if st["overflow"] or st["timeout"]:
+        raise RuntimeError(f"a batched frame was invalid: {st}")
+    n = views * len(groups)
+    return {"views_per_launch": views, "frames": n, "path": "FP16 colour, autotuned blend, CUDA graph",
+            "value": n / (batched_ms / 1000.0), "unit": "frames/s",
+            "same_frames_one_at_a_time": n / (single_ms / 1000.0)}
 
 
 def fp16_psnr(ctx, inst, inst16, cams, frame_ids, tau):

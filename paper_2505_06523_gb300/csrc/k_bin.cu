@@ -5,6 +5,8 @@
 // order, and each tile's range of the sorted pairs is found by boundary detection.  A pair key
 // carries, above the 20-bit tile id, the Gaussian's pixel box clipped to that tile (so that the
 // blend can skip pairs by their keys alone).
+#include <algorithm>
+
 #include "dev_common.cuh"
 
 namespace v3dg {
@@ -35,10 +37,11 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
   __shared__ uint32_t s_tbase[kExpTile];   // first (view, tile) id of the Gaussian's view
   __shared__ uint32_t s_scan[kExpThreads / 32 + 1];
   __shared__ uint32_t s_tile, s_base;
-  if (threadIdx.x == 0) s_tile = atomicAdd(frame + kTileCounters + tc_slot, 1u);
-  __syncthreads();
   const uint32_t n = min(frame[kVisible], cap);
   const uint32_t ntiles = (n + kExpTile - 1) / kExpTile;
+  for (;;) {   // persistent blocks: tiles in the order of an atomic counter
+  if (threadIdx.x == 0) s_tile = atomicAdd(frame + kTileCounters + tc_slot, 1u);
+  __syncthreads();
   const uint32_t tile = s_tile;
   if (tile >= ntiles) return;
   const uint32_t first = tile * kExpTile;
@@ -72,11 +75,9 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
   }
   __syncthreads();
   const uint32_t base = s_base;
-  if (uint64_t(base) + total > cap_pairs) {
-    if (threadIdx.x == 0) atomicOr(frame + kOverflow, 1u);
-    return;
-  }
-  for (uint32_t p = threadIdx.x; p < total; p += kExpThreads) {
+  const bool fits = uint64_t(base) + total <= cap_pairs;   // else the frame overflows: count, write nothing
+  if (!fits && threadIdx.x == 0) atomicOr(frame + kOverflow, 1u);
+  for (uint32_t p = threadIdx.x; fits && p < total; p += kExpThreads) {
     // last item j < items with s_off[j] <= p
     uint32_t lo = 0, hi = items;   // invariant: s_off[lo] <= p < s_off[hi] (s_off[items] >= total)
     while (hi - lo > 1) {
@@ -96,6 +97,8 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
     pk[base + p] = (s_tbase[lo] + ty * uint32_t(tiles_x) + tx) | (by0 << 20) | (by1 << 24) | ((bx0 >> 2) << 28) | ((bx1 >> 2) << 30);
     pv[base + p] = s_slot[lo];
   }
+  __syncthreads();   // the tile's shared data is consumed before the next tile reuses it
+  }  // next tile
 }
 
 // After duplication: the pair count that later stages use (none when the frame overflowed, so
@@ -104,15 +107,36 @@ __global__ void k_pairs_eff(uint32_t* frame, uint32_t cap_pairs) {
   frame[kPairsEff] = frame[kOverflow] ? 0u : min(frame[kPairs], cap_pairs);
 }
 
+// Tile ranges by boundary detection: each thread takes four consecutive sorted keys at a time
+// (one 16-byte load when the array is 16-byte aligned) and compares each with its neighbours.
 __global__ void __launch_bounds__(256)
 k_ranges(const uint32_t* __restrict__ tk, uint32_t cap_pairs, const uint32_t* __restrict__ frame,
          uint2* __restrict__ ranges, uint32_t n_tiles) {
   const uint32_t n = min(frame[kPairsEff], cap_pairs);
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const uint32_t t = tk[k] & kPairTileMask;
-    if (t >= n_tiles) continue;
-    if (k == 0 || (tk[k - 1] & kPairTileMask) != t) ranges[t].x = k;
-    if (k + 1 == n || (tk[k + 1] & kPairTileMask) != t) ranges[t].y = k + 1;
+  const uint32_t groups = (n + 3) / 4;
+  const bool aligned = (reinterpret_cast<uintptr_t>(tk) & 15u) == 0;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
+    const uint32_t k0 = 4 * g;
+    uint32_t t[6];   // tiles of keys k0 - 1 .. k0 + 4 (0xFFFFFFFF outside [0, n))
+    t[0] = k0 > 0 ? tk[k0 - 1] & kPairTileMask : 0xFFFFFFFFu;
+    if (aligned && k0 + 4 <= n) {
+      const uint4 v = *reinterpret_cast<const uint4*>(tk + k0);
+      t[1] = v.x & kPairTileMask;
+      t[2] = v.y & kPairTileMask;
+      t[3] = v.z & kPairTileMask;
+      t[4] = v.w & kPairTileMask;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[1 + i] = k0 + i < n ? tk[k0 + i] & kPairTileMask : 0xFFFFFFFFu;
+    }
+    t[5] = k0 + 4 < n ? tk[k0 + 4] & kPairTileMask : 0xFFFFFFFFu;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t k = k0 + i, tt = t[1 + i];
+      if (k >= n || tt >= n_tiles) continue;
+      if (t[i] != tt) ranges[tt].x = k;
+      if (t[i + 2] != tt) ranges[tt].y = k + 1;
+    }
   }
 }
 
@@ -121,8 +145,9 @@ k_ranges(const uint32_t* __restrict__ tk, uint32_t cap_pairs, const uint32_t* __
 cudaError_t launch_expand(const uint32_t* slots, const uint2* rect, uint32_t cap, uint32_t cap_pairs, int tiles_x,
                           const uint2* list, uint32_t inst_per_view, uint32_t tiles_per_view, uint32_t* pk,
                           uint32_t* pv, uint32_t* frame, uint32_t tc_slot, uint64_t* status, uint32_t epoch,
-                          cudaStream_t st) {
-  const uint32_t blocks = (cap + kExpTile - 1) / kExpTile;
+                          int sm_count, cudaStream_t st) {
+  // persistent grid: at most the resident blocks (8 of 256 threads per SM), whatever the capacity
+  const uint32_t blocks = std::min<uint32_t>((cap + kExpTile - 1) / kExpTile, uint32_t(sm_count) * 8u);
   if (blocks)
     k_expand<<<blocks, kExpThreads, 0, st>>>(slots, rect, cap, cap_pairs, tiles_x, list, inst_per_view, tiles_per_view,
                                              pk, pv, frame, tc_slot, status, epoch);

@@ -173,6 +173,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
       }
       if (q == 0) break;
       // stage the batch (kPer consecutive records per thread); each record's box within the item
+      // and the number of its pixels still accumulating
       uint32_t area[kPer], asum = 0;
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
@@ -191,8 +192,11 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
             int x0, x1, y0, y1;
             box_in_tile(r2, tx, ty, &x0, &x1, &y0, &y1);
             x0 = max(x0, qx0); x1 = min(x1, qx1); y0 = max(y0, qy0); y1 = min(y1, qy1);
-            if (x0 <= x1 && y0 <= y1) {
-              area[k] = uint32_t((x1 - x0 + 1) * (y1 - y0 + 1));
+            if (x0 <= x1 && y0 <= y1) {   // its pixels that are still accumulating
+              const uint32_t cols = (0xFFFFu >> (15 - x1)) & (0xFFFFu << x0);
+              uint32_t live = 0;
+              for (int y = y0; y <= y1; ++y) live += __popc((s_live[y >> 1] >> ((y & 1) * 16)) & cols);
+              area[k] = live;
               s_box[i] = uint32_t(x0) | (uint32_t(x1) << 8) | (uint32_t(y0) << 16) | (uint32_t(y1) << 24);
             }
           }
@@ -208,7 +212,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
       }
       if (threadIdx.x == 0) s_eoff[kBatch] = n_pairs;
       __syncthreads();
-      // record-parallel alpha test of the batch's (record, pixel) pairs, spread evenly
+      // record-parallel alpha test of the batch's (record, live pixel) pairs, spread evenly
       {
         // this thread's contiguous share of the pairs; its first record by binary search
         const uint32_t per = (n_pairs + kBlendThreads - 1) / kBlendThreads;
@@ -222,33 +226,40 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
           uint32_t j = lo;
           uint32_t e = e0;
           while (e < e1) {
-            // one record's run of pixels: (xx, yy) advance along the box rows
+            // one record's live pixels, row by row in column order
             const uint32_t eb = s_eoff[j], ee = s_eoff[j + 1];
-            if (ee == eb) {   // no pixel of this record in the item (its box was not written)
+            if (ee == eb) {   // no live pixel of this record in the item
               ++j;
               continue;
             }
             const uint32_t b = s_box[j];
-            const int x0 = int(b & 0xFFu), x1 = int((b >> 8) & 0xFFu), y0 = int((b >> 16) & 0xFFu);
-            const int w = x1 - x0 + 1;
-            const int k = int(e - eb);
-            int yy = y0 + k / w, xx = x0 + k % w;
+            const uint32_t x0 = b & 0xFFu, x1 = (b >> 8) & 0xFFu;
+            int yy = int((b >> 16) & 0xFFu);
+            const uint32_t cols = (0xFFFFu >> (15u - x1)) & (0xFFFFu << x0);
+            uint32_t m = (s_live[yy >> 1] >> ((yy & 1) * 16)) & cols;
+            uint32_t k = e - eb;   // live pixels of the record before this thread's share
+            while (k >= uint32_t(__popc(m))) {   // ends within the box: k < the record's live count
+              k -= __popc(m);
+              ++yy;
+              m = (s_live[yy >> 1] >> ((yy & 1) * 16)) & cols;
+            }
+            for (; k; --k) m &= m - 1;
             const uint32_t stop = min(e1, ee);
             const float4 g = s_g[j], c = s_c[j];
             const uint32_t bit = 1u << (j & 31);
-            uint32_t row = s_live[yy >> 1] >> ((yy & 1) * 16);   // live pixels of row yy
             for (; e < stop; ++e) {
-              if ((row >> xx) & 1u) {   // pixel still accumulating
-                const float l2a = log2_alpha(g, c, float(xx) + 0.5f, float(yy) + 0.5f);
-                if (kCount) ++n_eval;
-                if (l2a >= kLog2MinAlpha && fminf(0.999f, exp2f(l2a)) >= 1.f / 255.f)
-                  atomicOr(&s_mask[yy * 16 + xx][j >> 5], bit);
-              }
-              if (++xx > x1) {
-                xx = x0;
+              while (!m) {   // the next row with a live pixel of the box (there is one: e < ee)
                 ++yy;
-                row = yy < 16 ? s_live[yy >> 1] >> ((yy & 1) * 16) : 0u;
+                m = (s_live[yy >> 1] >> ((yy & 1) * 16)) & cols;
               }
+              const int xx = __ffs(m) - 1;
+              m &= m - 1;
+              const float l2a = log2_alpha(g, c, float(xx) + 0.5f, float(yy) + 0.5f);
+              if (kCount) ++n_eval;
+              // alpha = min(0.999, 2^l2a) >= 1/255; well above the threshold it holds without exp2
+              if (l2a >= kLog2MinAlpha + 1e-5f ||
+                  (l2a >= kLog2MinAlpha && fminf(0.999f, exp2f(l2a)) >= 1.f / 255.f))
+                atomicOr(&s_mask[yy * 16 + xx][j >> 5], bit);
             }
             ++j;
           }

@@ -6,6 +6,8 @@
 // warp, warps in order), publishes its per-digit counts, and looks back across earlier tiles
 // per digit (256 threads, one chain each, bounded waits) to find its global offsets.  The tile is
 // reordered by digit in shared memory first so that the global writes come out in runs.
+#include <algorithm>
+
 #include "dev_common.cuh"
 
 namespace v3dg {
@@ -120,12 +122,15 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   __shared__ uint32_t s_tile;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-  __syncthreads();
   const uint32_t n = min(*n_dev, cap);
   const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+  // persistent blocks: tiles in the order of an atomic counter, so every tile a look-back waits
+  // for is held by a running block
+  for (;;) {
+  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+  __syncthreads();
   const uint32_t tile = s_tile;
-  if (tile >= ntiles) return;  // the grid is sized by capacity: surplus blocks leave at once
+  if (tile >= ntiles) return;
   for (int i = tid; i < kWarps * kBins / 2; i += kSortThreads) reinterpret_cast<uint32_t*>(&s_wh[0][0])[i] = 0;
   if (tid < kBins) s_cnt[tid] = 0;
   __syncthreads();
@@ -203,9 +208,13 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     kout[dst] = k;
     vout[dst] = s_vals[p];
   }
+  __syncthreads();   // the tile's shared data is consumed before the next tile reuses it
+  }  // next tile
 }
 
 }  // namespace
+
+int g_sort_blocks_per_sm = 3;   // resident onesweep blocks per SM (set with the attributes)
 
 cudaError_t sort_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -213,6 +222,10 @@ cudaError_t sort_set_attributes() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<false>, kSortThreads, 0);
+  if (e == cudaSuccess && per_sm > 0) g_sort_blocks_per_sm = per_sm;
   return e;
 }
 
@@ -226,6 +239,8 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
   if (passes > 4) return cudaErrorInvalidValue;
   const uint32_t max_tiles = (cap + kSortTile - 1) / kSortTile;
   if (max_tiles > sc.max_tiles) return cudaErrorInvalidValue;
+  // persistent grid: the resident blocks, whatever the capacity (surplus blocks cost launches)
+  const uint32_t grid = std::min<uint32_t>(max_tiles, uint32_t(sm_count) * uint32_t(g_sort_blocks_per_sm));
   cudaError_t e = cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * kBins * passes, st);
   if (e != cudaSuccess) return e;
   k_hist<<<sm_count * 4, 256, 0, st>>>(k0, n_dev, cap, begin_bit, end_bit, passes, sc.hist);
@@ -239,10 +254,10 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
     if (epoch == 0) epoch = 1;
     const uint32_t ep = epoch;
     if (p == 0 && implicit_vals)
-      k_onesweep<true><<<max_tiles, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + 4 * kBins + kBins * p,
+      k_onesweep<true><<<grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + 4 * kBins + kBins * p,
                                                            sc.status, sc.tile_counters + p, ep, err_flag);
     else
-      k_onesweep<false><<<max_tiles, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + 4 * kBins + kBins * p,
+      k_onesweep<false><<<grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, dmask, sc.hist + 4 * kBins + kBins * p,
                                                             sc.status, sc.tile_counters + p, ep, err_flag);
     ++*launches;
     e = cudaGetLastError();

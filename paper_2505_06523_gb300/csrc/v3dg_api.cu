@@ -448,7 +448,7 @@ v3dg_status enqueue_render(Pipe* c, float* rgb, float* t_out) {
   const int tiles_view = k.tiles_x * k.tiles_y;
   CU(launch_expand(dslots, P<uint2>(c->d_rect), c->cap_slots, c->cap_pairs, k.tiles_x, P<uint2>(c->d_list),
                    c->n_views > 1 ? c->n_inst_frame / c->n_views : 0u, uint32_t(tiles_view), P<uint32_t>(c->d_pk0),
-                   P<uint32_t>(c->d_pv0), frame, 1, P<uint64_t>(c->d_status), next_epoch(c), c->stream));
+                   P<uint32_t>(c->d_pv0), frame, 1, P<uint64_t>(c->d_status), next_epoch(c), sm, c->stream));
   c->ctx->launches += 2;
 
   stage_event(c, kStageTileSort);

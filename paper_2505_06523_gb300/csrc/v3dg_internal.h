@@ -168,7 +168,7 @@ cudaError_t blend_set_attributes();
 cudaError_t launch_expand(const uint32_t* sorted_slots, const uint2* rect, uint32_t cap_slots, uint32_t cap_pairs,
                           int tiles_x, const uint2* list, uint32_t inst_per_view, uint32_t tiles_per_view,
                           uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* frame, uint32_t tile_counter_slot,
-                          uint64_t* status, uint32_t epoch, cudaStream_t st);
+                          uint64_t* status, uint32_t epoch, int sm_count, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const uint32_t* frame,
                           uint2* ranges, int n_tiles, int sm_count, cudaStream_t st);
 // work != nullptr: also count (evaluations, contributions) into work[0], work[1].
