@@ -550,22 +550,21 @@ FP32_LANES = 152 * 128
 BLEND_OPS_EVAL, BLEND_OPS_CONTRIB = 8, 10
 
 
+# DRAM bytes per unit from one ncu capture of the same kernel on the crowd's profiling case (2
+# assets, 300 instances): dram__bytes_read.sum + dram__bytes_write.sum of one launch / the units
+# of its frame.  Scaled to a full launch by the units processed (traffic grows with them).
+NCU_DRAM_PER_UNIT = {
+    "blend": (7.07, "pair", "profiles/k_blend_crowd_small.md"),      # (245.3 + 6.6) MB / 35.6M pairs
+    "project": (220.0, "slot", "profiles/k_project_crowd_small.md"),  # (2,996.9 + 855.5) MB / 17.5M slots
+}
+
+
 def roofline_for(stage, stage_ms, fs, peaks, peak_kind):
-    """Algorithmic work per launch of the dominant stage (means over the timed frames) over its
-    mean measured duration."""
-    if stage == "blend" and fs.get("blend_evals"):
-        ms = stage_ms["blend"]
-        ops = BLEND_OPS_EVAL * fs["blend_evals"] + BLEND_OPS_CONTRIB * fs["blend_contribs"]
-        mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = FP32_LANES * mhz * 1e6 / 1e12
-        achieved = ops / (ms / 1000.0) / 1e12
-        return {"stage": "blend", "kernel": "k_blend", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"derived: {FP32_LANES} FP32 lanes x {mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
-                "work": {"evals": fs["blend_evals"], "contribs": fs["blend_contribs"],
-                         "ops_per_eval": BLEND_OPS_EVAL, "ops_per_contrib": BLEND_OPS_CONTRIB, "ms": ms}}
+    """Algorithmic work per launch of every stage (means over the timed frames) over its mean
+    measured duration; the top-level fields are those of the dominant stage."""
     vis, pairs, nodes = fs["visible"], fs["pairs"], fs["render_nodes"]
     slots = nodes * 64
+    units = {"pair": pairs, "slot": slots}
     bytes_per = {
         # selection: the node tables are L2-resident; HBM traffic is the render list write
         "select": 8 * nodes,
@@ -573,21 +572,49 @@ def roofline_for(stage, stage_ms, fs, peaks, peak_kind):
         "project": 236 * slots + (48 + 8 + 4) * vis + 4 * (slots - vis),
         # depth sort: 4 passes of (key, value) read + write, plus the histogram read
         "depth_sort": slots * (4 * 16 + 4),
-        # binning: sorted slots + rects read, offsets written, pairs written
-        "bin": vis * (4 + 8 + 4 + 4 + 8) + pairs * 8,
+        # binning: sorted slots + pixel boxes read, pairs written
+        "bin": vis * (4 + 8) + pairs * 8,
         # tile sort: 2 passes of (key, value) read + write, plus the histogram read
         "tile_sort": pairs * (2 * 16 + 4),
         "ranges": pairs * 4 + 8 * 8160,
-        # blend: sorted values + 48-byte records per pair, the image written
-        "blend": pairs * (4 + 48) + WIDTH * HEIGHT * 16,
     }
+    hbm_peak = float(peaks["hbm_gbs"])
+    per_stage = {k: {"bound": "hbm", "gbs": v / (stage_ms[k] / 1000.0) / 1e9, "frac": v / (stage_ms[k] / 1000.0) / 1e9 / hbm_peak,
+                     "ms": stage_ms[k]} for k, v in bytes_per.items() if stage_ms.get(k)}
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = FP32_LANES * mhz * 1e6 / 1e12
+    if fs.get("blend_evals") and stage_ms.get("blend"):
+        ops = BLEND_OPS_EVAL * fs["blend_evals"] + BLEND_OPS_CONTRIB * fs["blend_contribs"]
+        tf = ops / (stage_ms["blend"] / 1000.0) / 1e12
+        per_stage["blend"] = {"bound": "alu", "tflops": tf, "frac": tf / alu_peak, "ms": stage_ms["blend"]}
+
+    def traffic(st):   # DRAM bytes per launch, from the ncu capture scaled by the units processed
+        if st not in NCU_DRAM_PER_UNIT:
+            return None
+        per, unit, _ = NCU_DRAM_PER_UNIT[st]
+        return per * units[unit]
+
+    def traffic_source(st):
+        if st not in NCU_DRAM_PER_UNIT:
+            return None
+        per, unit, src = NCU_DRAM_PER_UNIT[st]
+        return {"bytes_per_unit": per, "unit": unit, "from": src}
+
     ms = stage_ms[stage]
-    gbs = bytes_per[stage] / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
-    peak = float(peaks["hbm_gbs"])
-    return {"stage": stage, "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-            "traffic": None, "peak_source": peak_kind,
-            "per_stage_gbs": {k: (bytes_per[k] / (stage_ms[k] / 1000.0) / 1e9 if stage_ms[k] > 0 else None)
-                              for k in bytes_per}}
+    if stage == "blend" and "blend" in per_stage:
+        return {"stage": "blend", "kernel": "k_blend", "bound": "alu", "achieved": per_stage["blend"]["tflops"],
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": per_stage["blend"]["frac"], "traffic": traffic("blend"),
+                "traffic_source": traffic_source("blend"),
+                "peak_source": f"derived: {FP32_LANES} FP32 lanes x {mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+                "work": {"evals": fs["blend_evals"], "contribs": fs["blend_contribs"],
+                         "ops_per_eval": BLEND_OPS_EVAL, "ops_per_contrib": BLEND_OPS_CONTRIB, "ms": ms},
+                "per_stage": per_stage}
+    kernel = {"select": "k_select", "project": "k_project", "depth_sort": "k_onesweep", "bin": "k_expand",
+              "tile_sort": "k_onesweep", "ranges": "k_ranges"}[stage]
+    return {"stage": stage, "kernel": kernel, "bound": "hbm", "achieved": per_stage[stage]["gbs"], "peak": hbm_peak,
+            "unit": "GB/s", "frac": per_stage[stage]["frac"], "traffic": traffic(stage),
+            "traffic_source": traffic_source(stage), "peak_source": peak_kind,
+            "per_stage": per_stage}
 
 
 if __name__ == "__main__":
