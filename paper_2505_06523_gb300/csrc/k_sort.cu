@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kBins) k_hist_scan(const uint32_t* __restrict_
 }
 
 template <bool kImplicit>
-__global__ void __launch_bounds__(kSortThreads, 3)
+__global__ void __launch_bounds__(kSortThreads, 4)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
            uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev, uint32_t cap, int shift, uint32_t dmask,
            const uint32_t* __restrict__ gexcl, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
@@ -214,7 +214,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
 
 }  // namespace
 
-int g_sort_blocks_per_sm = 3;   // resident onesweep blocks per SM (set with the attributes)
+int g_sort_blocks_per_sm = 4;   // resident onesweep blocks per SM (set with the attributes)
 
 cudaError_t sort_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
