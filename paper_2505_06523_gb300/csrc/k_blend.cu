@@ -2,11 +2,11 @@
 //
 // One 256-thread block per 16x16 tile, or per 8x8 quadrant of a tile with a long list
 // (persistent blocks take work items heaviest-first: tiles differ in cost by orders of magnitude).
-// The tile's depth-ordered records are taken in batches of up to 256; each batch runs in two
-// phases:
-//  - record-parallel test: the batch's (record, pixel) pairs -- every pixel of the record's
-//    alpha >= 1/255 pixel box that is still accumulating -- are spread evenly over the threads;
-//    a pair whose alpha passes the skip rule sets the record's bit in that pixel's 256-bit mask;
+// The tile's depth-ordered records are taken in batches (128, 256 or 512 records); each batch runs
+// in two phases:
+//  - record-parallel test: each thread stages its own records and evaluates each at the pixels of
+//    its alpha >= 1/255 box that are still accumulating; a pixel where the skip rule passes gets
+//    the record's bit in its mask (one bit per record of the batch);
 //  - pixel-parallel blend: each thread walks its pixel's mask in record (= depth) order and
 //    blends exactly those records: a = min(0.999, 2^(na dx^2 + nb dx dy + nc dy^2 + log2 o)),
 //    stopping before T (1 - a) < 1e-4.
@@ -75,13 +75,10 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
   __shared__ float4 s_g[kBatch];                    // (u, v, na, nb) in this tile's pixel frame
   __shared__ float4 s_c[kBatch];                    // (nc, log2 o, r, g)
   __shared__ float s_b[kBatch];                     // b
-  __shared__ uint32_t s_box[kBatch];                // clipped box: x0 | x1 << 8 | y0 << 16 | y1 << 24
-  __shared__ uint32_t s_eoff[kBatch + 1];           // exclusive prefix of the box areas
   __shared__ uint32_t s_mask[kBlendThreads][kMaskWords];  // [pixel][record word]: contributing records
   __shared__ uint32_t s_live[kBlendWarps];          // unfinished pixels of the item, one word per row pair
   __shared__ uint32_t s_qslot[kBatch];              // the batch: slots of its records, in list order
   __shared__ uint32_t s_cnt[32];
-  __shared__ uint32_t s_scan[kBlendWarps + 1];
   __shared__ uint32_t s_next, s_resume, s_total;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;   // this thread's pixel in the tile
@@ -172,96 +169,40 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ items, co
         static_assert(kScan * kBlendWarps == 32, "one scan lane per (step, warp)");
       }
       if (q == 0) break;
-      // stage the batch (kPer consecutive records per thread); each record's box within the item
-      // and the number of its pixels still accumulating
-      uint32_t area[kPer], asum = 0;
+      // stage the batch (kPer consecutive records per thread) for the compositing phase, and test
+      // each of this thread's records at the pixels of its box that are still accumulating: a
+      // pixel where alpha >= 1/255 gets the record's bit in its mask
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
         const uint32_t i = threadIdx.x * kPer + k;
-        area[k] = 0;
-        if (i < q) {
-          const uint32_t slot = s_qslot[i];
-          if (slot < cap_slots) {
-            const float4* r = rec + 3 * size_t(slot);
-            const float4 r0 = r[0], r1 = r[1], r2 = r[2];
-            const uint32_t org = __float_as_uint(r2.y);
-            const float ox = float(16 * (tx - int(org & 0xFFFFu))), oy = float(16 * (ty - int(org >> 16)));
-            s_g[i] = make_float4(r0.x - ox, r0.y - oy, r0.z, r0.w);
-            s_c[i] = r1;
-            s_b[i] = r2.x;
-            int x0, x1, y0, y1;
-            box_in_tile(r2, tx, ty, &x0, &x1, &y0, &y1);
-            x0 = max(x0, qx0); x1 = min(x1, qx1); y0 = max(y0, qy0); y1 = min(y1, qy1);
-            if (x0 <= x1 && y0 <= y1) {   // its pixels that are still accumulating
-              const uint32_t cols = (0xFFFFu >> (15 - x1)) & (0xFFFFu << x0);
-              uint32_t live = 0;
-              for (int y = y0; y <= y1; ++y) live += __popc((s_live[y >> 1] >> ((y & 1) * 16)) & cols);
-              area[k] = live;
-              s_box[i] = uint32_t(x0) | (uint32_t(x1) << 8) | (uint32_t(y0) << 16) | (uint32_t(y1) << 24);
-            }
-          }
-        }
-        asum += area[k];
-      }
-      uint32_t n_pairs;
-      uint32_t eoff = block_exclusive_scan<kBlendWarps>(asum, s_scan, &n_pairs);
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {   // records q.. have area 0, so s_eoff[q] = n_pairs
-        if (threadIdx.x * kPer + k < uint32_t(kBatch)) s_eoff[threadIdx.x * kPer + k] = eoff;
-        eoff += area[k];
-      }
-      if (threadIdx.x == 0) s_eoff[kBatch] = n_pairs;
-      __syncthreads();
-      // record-parallel alpha test of the batch's (record, live pixel) pairs, spread evenly
-      {
-        // this thread's contiguous share of the pairs; its first record by binary search
-        const uint32_t per = (n_pairs + kBlendThreads - 1) / kBlendThreads;
-        const uint32_t e0 = min(threadIdx.x * per, n_pairs), e1 = min(e0 + per, n_pairs);
-        if (e0 < e1) {
-          uint32_t lo = 0, hi = q;   // last record with s_eoff[lo] <= e0 (s_eoff[q] = n_pairs > e0)
-          while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (s_eoff[mid] <= e0) lo = mid; else hi = mid;
-          }
-          uint32_t j = lo;
-          uint32_t e = e0;
-          while (e < e1) {
-            // one record's live pixels, row by row in column order
-            const uint32_t eb = s_eoff[j], ee = s_eoff[j + 1];
-            if (ee == eb) {   // no live pixel of this record in the item
-              ++j;
-              continue;
-            }
-            const uint32_t b = s_box[j];
-            const uint32_t x0 = b & 0xFFu, x1 = (b >> 8) & 0xFFu;
-            int yy = int((b >> 16) & 0xFFu);
-            const uint32_t cols = (0xFFFFu >> (15u - x1)) & (0xFFFFu << x0);
-            uint32_t m = (s_live[yy >> 1] >> ((yy & 1) * 16)) & cols;
-            uint32_t k = e - eb;   // live pixels of the record before this thread's share
-            while (k >= uint32_t(__popc(m))) {   // ends within the box: k < the record's live count
-              k -= __popc(m);
-              ++yy;
-              m = (s_live[yy >> 1] >> ((yy & 1) * 16)) & cols;
-            }
-            for (; k; --k) m &= m - 1;
-            const uint32_t stop = min(e1, ee);
-            const float4 g = s_g[j], c = s_c[j];
-            const uint32_t bit = 1u << (j & 31);
-            for (; e < stop; ++e) {
-              while (!m) {   // the next row with a live pixel of the box (there is one: e < ee)
-                ++yy;
-                m = (s_live[yy >> 1] >> ((yy & 1) * 16)) & cols;
-              }
-              const int xx = __ffs(m) - 1;
-              m &= m - 1;
-              const float l2a = log2_alpha(g, c, float(xx) + 0.5f, float(yy) + 0.5f);
-              if (kCount) ++n_eval;
-              // alpha = min(0.999, 2^l2a) >= 1/255; well above the threshold it holds without exp2
-              if (l2a >= kLog2MinAlpha + 1e-5f ||
-                  (l2a >= kLog2MinAlpha && fminf(0.999f, exp2f(l2a)) >= 1.f / 255.f))
-                atomicOr(&s_mask[yy * 16 + xx][j >> 5], bit);
-            }
-            ++j;
+        if (i >= q) continue;
+        const uint32_t slot = s_qslot[i];
+        if (slot >= cap_slots) continue;
+        const float4* r = rec + 3 * size_t(slot);
+        const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+        const uint32_t org = __float_as_uint(r2.y);
+        const float ox = float(16 * (tx - int(org & 0xFFFFu))), oy = float(16 * (ty - int(org >> 16)));
+        const float4 g = make_float4(r0.x - ox, r0.y - oy, r0.z, r0.w);
+        s_g[i] = g;
+        s_c[i] = r1;
+        s_b[i] = r2.x;
+        int x0, x1, y0, y1;
+        box_in_tile(r2, tx, ty, &x0, &x1, &y0, &y1);
+        x0 = max(x0, qx0); x1 = min(x1, qx1); y0 = max(y0, qy0); y1 = min(y1, qy1);
+        if (x0 > x1) continue;
+        const uint32_t cols = (0xFFFFu >> (15 - x1)) & (0xFFFFu << x0);
+        const uint32_t bit = 1u << (i & 31);
+        for (int yy = y0; yy <= y1; ++yy) {
+          uint32_t m = (s_live[yy >> 1] >> ((yy & 1) * 16)) & cols;
+          while (m) {
+            const int xx = __ffs(m) - 1;
+            m &= m - 1;
+            const float l2a = log2_alpha(g, r1, float(xx) + 0.5f, float(yy) + 0.5f);
+            if (kCount) ++n_eval;
+            // alpha = min(0.999, 2^l2a) >= 1/255; well above the threshold it holds without exp2
+            if (l2a >= kLog2MinAlpha + 1e-5f ||
+                (l2a >= kLog2MinAlpha && fminf(0.999f, exp2f(l2a)) >= 1.f / 255.f))
+              atomicOr(&s_mask[yy * 16 + xx][i >> 5], bit);
           }
         }
       }
