@@ -276,14 +276,15 @@ def main():
         ctx.render(rgb)
         ms, _ = ctx.stage_times(len(STAGES))
         stage_runs.append(ms)
-    # the same frames with the top-down selection (same cut and image; the select stage differs)
-    ctx.set_option(N.V3DG_OPT_SELECT_TOPDOWN, 1)
-    td_select = []
+    # the same frames with the flat selection (the default walks large scenes top-down; same cut
+    # and image, only the select stage differs)
+    ctx.set_option(N.V3DG_OPT_SELECT_TOPDOWN, 0)
+    flat_select = []
     for fid in timed_ids:
         ctx.select(cams[fid], args.tau)
         ctx.render(rgb)
-        td_select.append(ctx.stage_times(len(STAGES))[0][0])
-    ctx.set_option(N.V3DG_OPT_SELECT_TOPDOWN, 0)
+        flat_select.append(ctx.stage_times(len(STAGES))[0][0])
+    ctx.set_option(N.V3DG_OPT_SELECT_TOPDOWN, 2)
     ctx.set_option(N.V3DG_OPT_STAGE_TIMING, 0)
     stage_ms = {k: float(np.mean([r[i] for r in stage_runs])) for i, k in enumerate(STAGES)}
     # the blend's algorithmic work on the same frames (a separate, counting replay)
@@ -357,7 +358,7 @@ def main():
             "served": served,
             "gpu_launches": int(launches),
             "stages_ms": stage_ms,
-            "select_topdown_ms": float(np.mean(td_select)),
+            "select_flat_ms": float(np.mean(flat_select)),
             "frame_mean": {k: int(round(v)) for k, v in fs.items()},
             "stages_sum_ms": float(sum(stage_ms.values())),
             "roofline": roofline,
@@ -419,7 +420,7 @@ def _pcts(lat):
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
 
 
-DEFAULT_BLEND = {"batch": 256, "split_pairs": 0xFFFFFFFF}
+DEFAULT_BLEND = {"batch": 512, "split_pairs": 0xFFFFFFFF}
 
 
 def _blend_options(ctx, opts):
@@ -600,6 +601,13 @@ def roofline_for(stage, stage_ms, fs, peaks, peak_kind):
         per, unit, src = NCU_DRAM_PER_UNIT[st]
         return {"bytes_per_unit": per, "unit": unit, "from": src}
 
+    # the frame's roofline: each stage at its own bound (HBM bytes at the copy bandwidth, the blend's
+    # FP32 operations at the issue peak), summed, against the measured stage times
+    ideal_ms = sum(v / (hbm_peak * 1e9) * 1e3 for k, v in bytes_per.items() if k in per_stage)
+    if "blend" in per_stage:
+        ideal_ms += per_stage["blend"]["tflops"] * per_stage["blend"]["ms"] / alu_peak
+    frame = {"ideal_ms": ideal_ms, "measured_ms": sum(v["ms"] for v in per_stage.values()),
+             "frac": ideal_ms / max(sum(v["ms"] for v in per_stage.values()), 1e-9)}
     ms = stage_ms[stage]
     if stage == "blend" and "blend" in per_stage:
         return {"stage": "blend", "kernel": "k_blend", "bound": "alu", "achieved": per_stage["blend"]["tflops"],
@@ -608,13 +616,13 @@ def roofline_for(stage, stage_ms, fs, peaks, peak_kind):
                 "peak_source": f"derived: {FP32_LANES} FP32 lanes x {mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
                 "work": {"evals": fs["blend_evals"], "contribs": fs["blend_contribs"],
                          "ops_per_eval": BLEND_OPS_EVAL, "ops_per_contrib": BLEND_OPS_CONTRIB, "ms": ms},
-                "per_stage": per_stage}
+                "per_stage": per_stage, "frame": frame}
     kernel = {"select": "k_select", "project": "k_project", "depth_sort": "k_onesweep", "bin": "k_expand",
               "tile_sort": "k_onesweep", "ranges": "k_ranges"}[stage]
     return {"stage": stage, "kernel": kernel, "bound": "hbm", "achieved": per_stage[stage]["gbs"], "peak": hbm_peak,
             "unit": "GB/s", "frac": per_stage[stage]["frac"], "traffic": traffic(stage),
             "traffic_source": traffic_source(stage), "peak_source": peak_kind,
-            "per_stage": per_stage}
+            "per_stage": per_stage, "frame": frame}
 
 
 if __name__ == "__main__":

@@ -121,9 +121,11 @@ enum {
                                 level, testing only nodes whose parent's footprint exceeds tau_F and
                                 skipping subtrees that the visibility cull rejects as a whole; the
                                 cut is the same as the flat test of every node (F grows from a node
-                                to its parent, Sec. 3.4), in the same order.  Default 0 (flat). */
+                                to its parent, Sec. 3.4), in the same order.  0: the flat test of
+                                every (instance, node).  2 (default): top-down when that would be
+                                more than 8M tests, else flat. */
   V3DG_OPT_BLEND_BATCH = 9,    /* records the blend stages per batch in shared memory: 128, 256
-                                (default) or 512; the image does not depend on it */
+                                or 512 (default); the image does not depend on it */
   V3DG_OPT_GRAPHS = 10         /* 1: v3dg_select only stages the camera and instances, and
                                 v3dg_render runs the selection and the whole render as one CUDA
                                 graph, captured the first time a configuration (instance and view
@@ -253,11 +255,13 @@ v3dg_status v3dg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, uint64_t n, 
  * repeats its per-frame path (select, Sec. 3.4, then splat, Sec. 2.1) once per request.
  *
  * v3dg_server_start starts `slots` workers (1..64) on the context's device.  Each worker owns its
- * own stream and frame buffers (from cudaMalloc: the context's allocator is only ever called from
- * the thread that owns the context) and shares the loaded assets (load them all first).  Requests wait in arrival order; a free worker takes
- * the next one when the device-memory estimates of the requests in flight plus its own fit
- * `hbm_budget` bytes (0: no limit; a request is always admitted when none is in flight), so
- * requests overlap on the GPU as soon as they arrive.  Each frame is checked and re-run with
+ * own streams and frame buffers (from cudaMalloc: the context's allocator is only ever called from
+ * the thread that owns the context) and shares the loaded assets (load them all first).  Requests
+ * wait in arrival order; a free worker takes the next one when the device-memory estimates of the
+ * requests in flight plus its own fit `hbm_budget` bytes (0: no limit; a request is always
+ * admitted when none is in flight), so requests overlap on the GPU as soon as they arrive.  A
+ * request that starts while no other one is in flight runs on a high-priority stream, the others
+ * on low-priority streams, so a frame alone keeps its solo latency and later ones fill idle SMs.  Each frame is checked and re-run with
  * larger buffers on overflow, as v3dg_render does with V3DG_OPT_SYNC_CHECK.  While a server runs,
  * v3dg_set_option and v3dg_load_hierarchy return V3DG_EBUSY.  Status EBUSY if a server already
  * runs, ENOTFOUND if no asset is loaded. */

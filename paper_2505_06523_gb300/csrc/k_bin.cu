@@ -77,9 +77,12 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
   const uint32_t base = s_base;
   const bool fits = uint64_t(base) + total <= cap_pairs;   // else the frame overflows: count, write nothing
   if (!fits && threadIdx.x == 0) atomicOr(frame + kOverflow, 1u);
+  uint32_t lo = 0;   // the owner of this thread's previous position: owners only move forward
   for (uint32_t p = threadIdx.x; fits && p < total; p += kExpThreads) {
-    // last item j < items with s_off[j] <= p
-    uint32_t lo = 0, hi = items;   // invariant: s_off[lo] <= p < s_off[hi] (s_off[items] >= total)
+    // last item j < items with s_off[j] <= p; each Gaussian has at least one pair, so the owner
+    // of p lies within 256 items of the owner of p - 256
+    uint32_t hi = min(lo + uint32_t(kExpThreads) + 1u, items);   // invariant: s_off[lo] <= p < s_off[hi]
+    if (s_off[hi] <= p) hi = items;   // (only when hi was clipped below items: s_off[items] >= total > p)
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) >> 1;
       if (s_off[mid] <= p) lo = mid; else hi = mid;

@@ -115,8 +115,8 @@ struct v3dg_ctx {
   bool sync_check = true, stage_timing = false, count_work = false;
   uint32_t split_pairs = 0xFFFFFFFFu;   // long-tile split threshold (none by default)
   bool attr_fp16 = false;   // store opacity and SH of the next loaded assets as float16
-  bool topdown = false;     // select level by level from the roots (same cut as the flat kernel)
-  int blend_batch = 256;    // records staged per blend batch: 128, 256 or 512
+  int topdown = 2;          // 0 flat, 1 level by level from the roots (same cut), 2 top-down for large scenes
+  int blend_batch = 512;    // records staged per blend batch: 128, 256 or 512
   bool graphs = false;      // capture each frame's launches once and replay them as a CUDA graph
   Pipe main;
   Server* server = nullptr;
@@ -382,10 +382,21 @@ v3dg_status topdown_buffers(Pipe* c, TopDown* td) {
   return V3DG_OK;
 }
 
+// Whether this frame's selection walks the trees top-down: always (option 1), never (0), or when
+// the flat kernel would test more than kTopDownTests (instance, node) pairs (2, the default; on
+// small scenes the walk's one launch per level costs more than it saves).
+constexpr uint64_t kTopDownTests = 8u << 20;
+bool use_topdown(const Pipe* c) {
+  if (c->ctx->topdown != 2) return c->ctx->topdown == 1;
+  uint64_t max_nodes = 0;
+  for (const AssetHost& a : c->ctx->assets) max_nodes = std::max<uint64_t>(max_nodes, a.n_nodes);
+  return uint64_t(c->n_inst_frame) * max_nodes > kTopDownTests;
+}
+
 // Selection into `out` (mode 0: the render list, mode 1: the cut), flat or top-down.
 v3dg_status launch_selection(Pipe* c, int mode, uint2* out, uint32_t cap, uint32_t* frame) {
   if (!c->n_inst_frame) return V3DG_OK;
-  if (c->ctx->topdown) {
+  if (use_topdown(c)) {
     TopDown td{};
     ST(topdown_buffers(c, &td));
     int nl = 0;
@@ -536,7 +547,7 @@ std::vector<uint64_t> graph_key(Pipe* c, float* rgb, float* t_out) {
   const v3dg_ctx* ctx = c->ctx;
   std::vector<uint64_t> k = {c->n_inst_frame, c->n_views, uint64_t(c->node_blocks), c->cap_nodes, c->cap_pairs,
                              c->cap_slots, c->status_words, uint64_t(uintptr_t(rgb)), uint64_t(uintptr_t(t_out)),
-                             uint64_t(ctx->topdown), uint64_t(ctx->blend_batch), ctx->split_pairs,
+                             uint64_t(use_topdown(c)), uint64_t(ctx->blend_batch), ctx->split_pairs,
                              uint64_t(ctx->count_work), uint64_t(c->color_formats), ctx->assets.size(),
                              uint64_t(uintptr_t(ctx->d_assets.p))};
   const DevBuf* bufs[] = {&c->d_inst, &c->d_frame, &c->d_misc, &c->d_list, &c->d_ref, &c->d_keys0, &c->d_keys1,
@@ -558,7 +569,7 @@ v3dg_status run_graph_frame(Pipe* c, float* rgb, float* t_out, bool sync) {
   const int n_tiles = c->cc.tiles_x * c->cc.tiles_y * int(c->n_views);
   ST(ensure(c, c->d_ranges, sizeof(uint2) * size_t(n_tiles)));
   ST(ensure(c, c->d_order, sizeof(uint32_t) * (4 * size_t(n_tiles) + 1)));
-  if (c->ctx->topdown) {
+  if (use_topdown(c)) {
     TopDown td{};
     ST(topdown_buffers(c, &td));
   }
@@ -941,7 +952,10 @@ v3dg_status v3dg_set_option(v3dg_ctx* ctx, int option, int64_t value) {
     case V3DG_OPT_STAGE_TIMING: ctx->stage_timing = value != 0; break;
     case V3DG_OPT_COUNT_WORK: ctx->count_work = value != 0; break;
     case V3DG_OPT_ATTR_FP16: ctx->attr_fp16 = value != 0; break;
-    case V3DG_OPT_SELECT_TOPDOWN: ctx->topdown = value != 0; break;
+    case V3DG_OPT_SELECT_TOPDOWN:
+      if (value < 0 || value > 2) return fail(c, V3DG_EINVAL, "top-down selection: 0, 1 or 2");
+      ctx->topdown = int(value);
+      break;
     case V3DG_OPT_GRAPHS: ctx->graphs = value != 0; break;
     case V3DG_OPT_BLEND_BATCH:
       if (value != 128 && value != 256 && value != 512) return fail(c, V3DG_EINVAL, "blend batch must be 128, 256 or 512");
