@@ -555,8 +555,9 @@ BLEND_OPS_EVAL, BLEND_OPS_CONTRIB = 8, 10
 # assets, 300 instances): dram__bytes_read.sum + dram__bytes_write.sum of one launch / the units
 # of its frame.  Scaled to a full launch by the units processed (traffic grows with them).
 NCU_DRAM_PER_UNIT = {
-    "blend": (7.07, "pair", "profiles/k_blend_crowd_small.md"),      # (245.3 + 6.6) MB / 35.6M pairs
-    "project": (220.0, "slot", "profiles/k_project_crowd_small.md"),  # (2,996.9 + 855.5) MB / 17.5M slots
+    "blend": (7.21, "pair", "profiles/k_blend_crowd_small.md"),      # (250.3 + 6.2) MB / 35.6M pairs
+    "project": (220.0, "slot", "profiles/k_project_crowd_small.md"),  # (2,999.5 + 854.7) MB / 17.5M slots
+    "bin": (11.84, "pair", "profiles/k_expand_crowd_small.md"),       # (175.0 + 246.1) MB / 35.6M pairs
 }
 
 
