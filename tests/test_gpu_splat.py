@@ -330,3 +330,26 @@ def test_graph_frames_match_launch_by_launch(Context, tiny_asset, small_asset):
     assert float(np.abs(out[0][0][0]).sum()) > 0
     for (r0, t0, p0, n0), (r1, t1, p1, n1) in zip(out[0], out[1]):
         assert (r0 == r1).all() and (t0 == t1).all() and p0 == p1 and n0 == n1
+
+
+def test_views_topdown_graph_batch512_together(Context, tiny_asset, small_asset):
+    """Batched views, top-down selection, CUDA-graph frames and 512-record blend batches at once:
+    every view's image is that of the view rendered alone with the plain settings, bit for bit."""
+    from paper_2505_06523_gb300._native import V3DG_OPT_BLEND_BATCH, V3DG_OPT_GRAPHS, V3DG_OPT_SELECT_TOPDOWN
+    inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+    assets = [tiny_asset, small_asset]
+    cams = [scenes.crowd_camera(t, 320, 180) for t in (5, 60, 200)]
+    singles = [_frame(Context, assets, inst, cam, 1.0, {V3DG_OPT_SELECT_TOPDOWN: 0, V3DG_OPT_BLEND_BATCH: 256})
+               for cam in cams]
+    with Context(0) as ctx:
+        for k, v in ((V3DG_OPT_SELECT_TOPDOWN, 1), (V3DG_OPT_GRAPHS, 1), (V3DG_OPT_BLEND_BATCH, 512)):
+            ctx.set_option(k, v)
+        for a in assets:
+            ctx.load_hierarchy(a)
+        ctx.set_instances(inst)
+        for _ in range(2):   # the second round replays the captured graph
+            ctx.select_views(cams, 1.0)
+            rgb, T = ctx.render(want_T=True)
+            rgb, T = rgb.cpu().numpy(), T.cpu().numpy()
+            for v, one in enumerate(singles):
+                assert (rgb[v] == one["rgb"]).all() and (T[v] == one["T"]).all(), v
