@@ -35,6 +35,11 @@ __device__ __forceinline__ void chain_publish(uint64_t* status, uint32_t stride,
   st_status(status + size_t(tile) * stride, pack_status(epoch, tile == 0 ? kFlagPrefix : kFlagAgg, agg));
 }
 
+//
+// The walk reads kW earlier tiles' words per round with independent loads, so a walk over n
+// tiles costs about n / kW memory latencies instead of n: walks are long when tiles reach their
+// look-back out of order (a tile passes every earlier one that has only its aggregate).
+template <int kW = 1>
 __device__ __forceinline__ uint32_t chain_lookback(uint64_t* status, uint32_t stride, uint32_t tile, uint32_t agg,
                                                    uint32_t epoch, uint32_t* err) {
   if (tile == 0) return 0;
@@ -42,21 +47,74 @@ __device__ __forceinline__ uint32_t chain_lookback(uint64_t* status, uint32_t st
   int64_t j = int64_t(tile) - 1;
   uint32_t spins = 0;
   while (j >= 0) {
-    const uint64_t s = ld_status(status + size_t(j) * stride);
-    const uint32_t flag = uint32_t(s >> 32) & 3u;
-    if (uint32_t(s >> 34) != epoch || flag == 0) {
+    uint64_t s[kW];
+#pragma unroll
+    for (int w = 0; w < kW; ++w) s[w] = j - w >= 0 ? ld_status(status + size_t(j - w) * stride) : 0;
+    // consume the words in order, up to the first inclusive prefix or the first unwritten word
+    int used = 0;
+    bool done = false, wait = false;
+#pragma unroll
+    for (int w = 0; w < kW; ++w) {
+      if (done || wait || j - w < 0) continue;
+      const uint32_t flag = uint32_t(s[w] >> 32) & 3u;
+      if (uint32_t(s[w] >> 34) != epoch || flag == 0) {
+        wait = true;
+        continue;
+      }
+      excl += uint32_t(s[w]);
+      ++used;
+      done = flag == kFlagPrefix;
+    }
+    if (done) break;
+    j -= used;
+    if (wait) {
       if (++spins > kSpinLimit) {
         atomicOr(err, 1u);
         break;
       }
       if (spins > 32) __nanosleep(32);
-      continue;
     }
-    excl += uint32_t(s);
-    if (flag == kFlagPrefix) break;
-    --j;
   }
   st_status(status + size_t(tile) * stride, pack_status(epoch, kFlagPrefix, excl + agg));
+  return excl;
+}
+
+// The look-back of one chain by a whole warp (all 32 lanes call it, converged): lane i reads the
+// word of tile j - i, so each round covers 32 tiles; the nearest inclusive prefix or unwritten
+// word ends the round.  Returns the exclusive prefix in every lane; lane 0 publishes.
+__device__ __forceinline__ uint32_t chained_exclusive_warp(uint64_t* status, uint32_t tile, uint32_t agg,
+                                                           uint32_t epoch, uint32_t* err) {
+  const uint32_t lane = threadIdx.x & 31u;
+  if (lane == 0) chain_publish(status, 1, tile, agg, epoch);
+  if (tile == 0) return 0;
+  uint32_t excl = 0, spins = 0;
+  int64_t j = int64_t(tile) - 1;
+  for (;;) {
+    const int64_t q = j - int64_t(lane);
+    // before tile 0 (never reached: tile 0 publishes an inclusive prefix) reads as a zero prefix
+    const uint64_t s = q >= 0 ? ld_status(status + q) : pack_status(epoch, kFlagPrefix, 0);
+    const uint32_t flag = uint32_t(s >> 32) & 3u;
+    const bool ready = uint32_t(s >> 34) == epoch && flag != 0;
+    const uint32_t not_ready = __ballot_sync(0xffffffffu, !ready);
+    const uint32_t prefix = __ballot_sync(0xffffffffu, ready && flag == kFlagPrefix);
+    const uint32_t first_wait = not_ready ? uint32_t(__ffs(not_ready) - 1) : 32u;
+    const uint32_t first_prefix = prefix ? uint32_t(__ffs(prefix) - 1) : 32u;
+    const uint32_t take = first_prefix < first_wait ? first_prefix + 1 : first_wait;
+    uint32_t v = lane < take ? uint32_t(s) : 0u;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    excl += v;
+    if (first_prefix < first_wait) break;
+    j -= take;
+    if (take == 0) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) atomicOr(err, 1u);
+        break;
+      }
+      if (spins > 32) __nanosleep(32);
+    }
+  }
+  if (lane == 0) st_status(status + tile, pack_status(epoch, kFlagPrefix, excl + agg));
   return excl;
 }
 

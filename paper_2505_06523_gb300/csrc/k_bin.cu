@@ -68,10 +68,13 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
     s_off[threadIdx.x * kExpItems + i] = ex;
     ex += c[i];
   }
-  if (threadIdx.x == 0) {
-    s_off[kExpTile] = total;
-    s_base = chained_exclusive(status, 1, tile, total, epoch, frame + kTimeout);
-    if (tile == ntiles - 1) frame[kPairs] = s_base + total;
+  if (threadIdx.x < 32) {   // warp 0: the look-back, 32 tiles per round
+    const uint32_t b = chained_exclusive_warp(status, tile, total, epoch, frame + kTimeout);
+    if (threadIdx.x == 0) {
+      s_off[kExpTile] = total;
+      s_base = b;
+      if (tile == ntiles - 1) frame[kPairs] = b + total;
+    }
   }
   __syncthreads();
   const uint32_t base = s_base;

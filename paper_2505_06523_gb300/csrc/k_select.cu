@@ -138,9 +138,11 @@ k_select(const InstFrame* __restrict__ inst, int n_inst, const AssetDev* __restr
     const uint32_t ex = incl - a - b;
     s_cnt[2 * lane] = ex;
     s_cnt[2 * lane + 1] = ex + a;
+    const uint32_t block_total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t block_excl = chained_exclusive_warp(status, tile, block_total, epoch, frame + kTimeout);
     if (lane == 31) {
       s_total = incl;
-      s_excl = chained_exclusive(status, 1, tile, incl, epoch, frame + kTimeout);
+      s_excl = block_excl;
       if (mode == 1) {
         uint32_t g = 0;
         for (int w = 0; w < kSelWarps; ++w) g += s_gauss[w];
@@ -262,7 +264,10 @@ k_td_compact(const uint32_t* __restrict__ bitmap, uint32_t n_words, uint32_t wpi
   uint32_t word = w < n_words ? bitmap[w] : 0u;
   uint32_t total;
   const uint32_t ex = block_exclusive_scan<kSelWarps>(__popc(word), s_scan, &total);
-  if (threadIdx.x == 0) s_excl = chained_exclusive(status, 1, tile, total, epoch, frame + kTimeout);
+  if (threadIdx.x < 32) {
+    const uint32_t e = chained_exclusive_warp(status, tile, total, epoch, frame + kTimeout);
+    if (threadIdx.x == 0) s_excl = e;
+  }
   __syncthreads();
   uint32_t pos = s_excl + ex;
   const uint32_t ii = w / wpi, nb = (w % wpi) * 32u;

@@ -3,9 +3,10 @@
 // One histogram kernel reads the keys once and counts all digit passes; then each 8-bit pass is
 // a single kernel: a block takes the next 4096-key tile (virtual id from an atomic counter),
 // ranks its keys per digit with warp match/popc (stable: item-major then lane order within a
-// warp, warps in order), publishes its per-digit counts, and looks back across earlier tiles
-// per digit (256 threads, one chain each, bounded waits) to find its global offsets.  The tile is
-// reordered by digit in shared memory first so that the global writes come out in runs.
+// warp, warps in order), publishes its per-digit counts, reorders the tile by digit in shared
+// memory (so that the global writes come out in runs), and looks back across earlier tiles per
+// digit (one thread per digit, 4 status words per round, bounded waits) to find its global
+// offsets.
 #include <algorithm>
 
 #include "dev_common.cuh"
@@ -14,6 +15,7 @@ namespace v3dg {
 namespace {
 
 constexpr int kBins = 256;
+constexpr int kLookback = 4;   // status words read per look-back round
 constexpr int kWarps = kSortThreads / 32;
 static_assert(kSortThreads >= kBins, "one thread per digit");
 
@@ -150,7 +152,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   for (int i = 0; i < kSortItems; ++i)
     if (base + i * 32 + lane < n) atomicAdd(&s_cnt[(key[i] >> shift) & dmask], 1u);
   __syncthreads();
-  if (tid < kBins) chain_publish(status + tid, kBins, tile, s_cnt[tid], epoch);
+  if (tid <= dmask) chain_publish(status + tid, kBins, tile, s_cnt[tid], epoch);   // digits of the pass only
   // warp-level stable ranking: item-major, then lane order
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
@@ -182,13 +184,10 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   }
   uint32_t total;
   const uint32_t start = block_exclusive_scan<kWarps>(cnt, s_scan, &total);
-  if (tid < kBins) {
-    s_start[tid] = start;
-    const uint32_t excl = chain_lookback(status + tid, kBins, tile, cnt, epoch, err);
-    s_goff[tid] = int32_t(gexcl[tid] + excl) - int32_t(start);
-  }
+  if (tid < kBins) s_start[tid] = start;
   __syncthreads();
-  // reorder the tile by digit in shared memory
+  // reorder the tile by digit in shared memory (before the look-back, which needs none of the
+  // tile's registers and gets the earlier tiles more time to publish)
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t idx = base + i * 32 + lane;
@@ -198,6 +197,10 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
       s_keys[pos] = key[i];
       s_vals[pos] = val[i];
     }
+  }
+  if (tid <= dmask) {   // (the digit's count and start reloaded: no registers held over the reorder)
+    const uint32_t excl = chain_lookback<kLookback>(status + tid, kBins, tile, s_cnt[tid], epoch, err);
+    s_goff[tid] = int32_t(gexcl[tid] + excl) - int32_t(s_start[tid]);
   }
   __syncthreads();
   const uint32_t valid = min(uint32_t(kSortTile), n - tile * kSortTile);
