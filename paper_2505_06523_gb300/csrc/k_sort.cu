@@ -108,22 +108,6 @@ __global__ void __launch_bounds__(kBins) k_hist_scan(const uint32_t* __restrict_
   }
 }
 
-// Loads a tile's keys (and values) warp-striped: item i of lane l of warp w is element
-// tile * kSortTile + w * 512 + i * 32 + l.  Past the end: key 0xFFFFFFFF, not ranked.
-template <bool kImplicit>
-__device__ __forceinline__ void load_tile(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                          uint32_t tile, uint32_t n, uint32_t (&key)[kSortItems],
-                                          uint32_t (&val)[kSortItems]) {
-  const uint32_t base = tile * kSortTile + (threadIdx.x >> 5) * (kSortItems * 32) + (threadIdx.x & 31);
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    const uint32_t idx = base + i * 32;
-    const bool ok = idx < n;
-    key[i] = ok ? kin[idx] : 0xFFFFFFFFu;
-    val[i] = kImplicit ? idx : (ok ? vin[idx] : 0u);
-  }
-}
-
 template <bool kImplicit>
 __global__ void __launch_bounds__(kSortThreads, 4)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
@@ -137,28 +121,31 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   __shared__ int32_t s_goff[kBins];          // global destination offset minus local start
   __shared__ uint32_t s_cnt[kBins];          // the tile's digit counts
   __shared__ uint32_t s_scan[kWarps + 1];
-  __shared__ uint32_t s_tile, s_next;
+  __shared__ uint32_t s_tile;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t n = min(*n_dev, cap);
   const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
-  // Persistent blocks take tiles in the order of an atomic counter.  A block claims its next tile
-  // while it works on the current one and loads the next tile's keys during the current tile's
-  // look-back and write-out.  Every tile a look-back waits for is still held by a running block:
-  // the lowest unfinished tile is always a block's current tile (a block's next tile is higher
-  // than its current one), and its look-back needs only finished tiles.
+  // persistent blocks: tiles in the order of an atomic counter, so every tile a look-back waits
+  // for is held by a running block
+  for (;;) {
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
   __syncthreads();
-  uint32_t tile = s_tile;
+  const uint32_t tile = s_tile;
   if (tile >= ntiles) return;
-  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
-  load_tile<kImplicit>(kin, vin, tile, n, key, val);
-  for (;;) {
   for (int i = tid; i < kWarps * kBins / 2; i += kSortThreads) reinterpret_cast<uint32_t*>(&s_wh[0][0])[i] = 0;
   if (tid < kBins) s_cnt[tid] = 0;
-  if (tid == 0) s_next = atomicAdd(tile_counter, 1u);
   __syncthreads();
   const uint32_t base = tile * kSortTile + warp * (kSortItems * 32);
+
+  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t idx = base + i * 32 + lane;
+    const bool ok = idx < n;
+    key[i] = ok ? kin[idx] : 0xFFFFFFFFu;
+    val[i] = kImplicit ? idx : (ok ? vin[idx] : 0u);
+  }
   // the tile's digit counts first, published at once, so that later tiles' look-backs find them
   // while this tile is still ranking
 #pragma unroll
@@ -211,9 +198,6 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
       s_vals[pos] = val[i];
     }
   }
-  // the next tile's loads go out now and land during the look-back and the write-out
-  const uint32_t next = s_next;
-  if (next < ntiles) load_tile<kImplicit>(kin, vin, next, n, key, val);
   if (tid <= dmask) {   // (the digit's count and start reloaded: no registers held over the reorder)
     const uint32_t excl = chain_lookback<kLookback>(status + tid, kBins, tile, s_cnt[tid], epoch, err);
     s_goff[tid] = int32_t(gexcl[tid] + excl) - int32_t(s_start[tid]);
@@ -228,8 +212,6 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     vout[dst] = s_vals[p];
   }
   __syncthreads();   // the tile's shared data is consumed before the next tile reuses it
-  if (next >= ntiles) return;
-  tile = next;
   }  // next tile
 }
 
