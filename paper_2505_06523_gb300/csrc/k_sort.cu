@@ -2,8 +2,8 @@
 //
 // One histogram kernel reads the keys once and counts all digit passes; then each 8-bit pass is
 // a single kernel: a block takes the next 4096-key tile (virtual id from an atomic counter),
-// ranks its keys per digit with warp match/popc (stable: item-major then lane order within a
-// warp, warps in order), publishes its per-digit counts, reorders the tile by digit in shared
+// ranks its keys per digit within each warp (stable: item-major then lane order within a warp,
+// warps in order), publishes its per-digit counts, reorders the tile by digit in shared
 // memory (so that the global writes come out in runs), and looks back across earlier tiles per
 // digit (one thread per digit, 4 status words per round, bounded waits) to find its global
 // offsets.
@@ -122,10 +122,12 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   __shared__ uint32_t s_cnt[kBins];          // the tile's digit counts
   __shared__ uint32_t s_scan[kWarps + 1];
   __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_match[kWarps][kBins];   // per warp, the lanes holding each digit (zero between items)
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t n = min(*n_dev, cap);
   const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+  for (int i = tid; i < kWarps * kBins; i += kSortThreads) (&s_match[0][0])[i] = 0u;
   // persistent blocks: tiles in the order of an atomic counter, so every tile a look-back waits
   // for is held by a running block
   for (;;) {
@@ -153,7 +155,10 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     if (base + i * 32 + lane < n) atomicAdd(&s_cnt[(key[i] >> shift) & dmask], 1u);
   __syncthreads();
   if (tid <= dmask) chain_publish(status + tid, kBins, tile, s_cnt[tid], epoch);   // digits of the pass only
-  // warp-level stable ranking: item-major, then lane order
+  // warp-level stable ranking: item-major, then lane order.  The lanes that share a digit come
+  // from a shared-memory OR of lane bits (measured faster than match.any), or are the whole warp
+  // when every lane has the same digit (common in the high digits of the depth keys, where the
+  // OR would serialise on one word).
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t idx = base + i * 32 + lane;
@@ -162,11 +167,21 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     rank[i] = 0;
     if (ok) {
       const uint32_t d = (key[i] >> shift) & dmask;
-      const uint32_t peers = __match_any_sync(live, d);
+      const uint32_t d0 = __shfl_sync(live, d, __ffs(live) - 1);
+      const bool same = __all_sync(live, d == d0);   // (uniform over the live lanes)
+      uint32_t peers = live;
+      if (!same) {
+        atomicOr(&s_match[warp][d], 1u << lane);
+        __syncwarp(live);
+        peers = s_match[warp][d];
+      }
       const uint32_t before = __popc(peers & lanemask_lt());
       const uint32_t cur = s_wh[warp][d];
       __syncwarp(live);
-      if (before == 0) s_wh[warp][d] = uint16_t(cur + __popc(peers));
+      if (before == 0) {   // the digit's first lane: advance the warp's count, clear the lane bits
+        s_wh[warp][d] = uint16_t(cur + __popc(peers));
+        if (!same) s_match[warp][d] = 0u;
+      }
       __syncwarp(live);
       rank[i] = cur + before;
     }
