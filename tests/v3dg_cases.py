@@ -5,7 +5,7 @@ import numpy as np
 
 import oracle
 
-# tolerances of the per-Gaussian records (the image bar is the max-abs 1e-4 of the benchmark spec)
+# tolerances of the per-Gaussian records (the image bar is a max abs error of 1e-4 per channel)
 U_ABS_PX = 2e-3          # screen mean, px
 CONIC_REL = 2e-3         # relative to the largest conic entry
 RGB_ABS = 2e-5
