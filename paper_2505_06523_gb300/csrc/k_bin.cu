@@ -20,12 +20,14 @@ __device__ __forceinline__ uint32_t rect_area(const uint2 b) {
 }
 
 constexpr int kExpThreads = 256, kExpItems = 4, kExpTile = kExpThreads * kExpItems;
+constexpr uint32_t kExpWarps = kExpThreads / 32;
 
 // One pass over the depth-sorted visible Gaussians: each block takes 1024 of them, scans their
 // tile counts, finds its first pair position with a bounded look-back and then writes its pairs
-// cooperatively: output position p belongs to the Gaussian j with off[j] <= p < off[j + 1]
-// (binary search in shared memory), so large Gaussians are spread over the whole block and the
-// writes are contiguous.
+// cooperatively: output position p belongs to the Gaussian j with off[j] <= p < off[j + 1], each
+// warp takes one contiguous range of positions and follows the owners forward (one binary search
+// per warp and tile), so large Gaussians are spread over the whole block and the writes are
+// contiguous.
 __global__ void __launch_bounds__(kExpThreads)
 k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uint32_t cap, uint32_t cap_pairs,
          int tiles_x, const uint2* __restrict__ list, uint32_t inst_per_view, uint32_t tiles_per_view,
@@ -37,6 +39,7 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
   __shared__ uint32_t s_tbase[kExpTile];   // first (view, tile) id of the Gaussian's view
   __shared__ uint32_t s_scan[kExpThreads / 32 + 1];
   __shared__ uint32_t s_tile, s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t n = min(frame[kVisible], cap);
   const uint32_t ntiles = (n + kExpTile - 1) / kExpTile;
   for (;;) {   // persistent blocks: tiles in the order of an atomic counter
@@ -80,16 +83,37 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
   const uint32_t base = s_base;
   const bool fits = uint64_t(base) + total <= cap_pairs;   // else the frame overflows: count, write nothing
   if (!fits && threadIdx.x == 0) atomicOr(frame + kOverflow, 1u);
-  uint32_t lo = 0;   // the owner of this thread's previous position: owners only move forward
-  for (uint32_t p = threadIdx.x; fits && p < total; p += kExpThreads) {
-    // last item j < items with s_off[j] <= p; each Gaussian has at least one pair, so the owner
-    // of p lies within 256 items of the owner of p - 256
-    uint32_t hi = min(lo + uint32_t(kExpThreads) + 1u, items);   // invariant: s_off[lo] <= p < s_off[hi]
-    if (s_off[hi] <= p) hi = items;   // (only when hi was clipped below items: s_off[items] >= total > p)
+  // Each warp writes one contiguous range of the tile's pairs, 32 positions per step.  The owner
+  // of position p is the last item j with s_off[j] <= p.  Items start at distinct positions (each
+  // Gaussian has at least one pair), so at most 32 items start within a step: with `ob` the owner
+  // of the position before the step, lane i checks item ob + 1 + i, the warp ORs the start
+  // offsets that fall in the step into one mask, and a lane's owner is ob plus the starts at or
+  // before its position.
+  const uint32_t per_warp = ((total + kExpWarps * 32u - 1u) / (kExpWarps * 32u)) * 32u;
+  const uint32_t pw0 = min(uint32_t(warp) * per_warp, total), pw1 = min(pw0 + per_warp, total);
+  int ob = -1;   // owner of pw0 - 1 (none before position 0)
+  if (fits && pw0 > 0) {   // binary search, the same in every lane: s_off[lo] <= pw0 - 1 < s_off[hi]
+    uint32_t lo = 0, hi = items;   // (s_off[0] = 0, s_off[items] = total)
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (s_off[mid] <= p) lo = mid; else hi = mid;
+      if (s_off[mid] <= pw0 - 1u) lo = mid; else hi = mid;
     }
+    ob = int(lo);
+  }
+  for (uint32_t p0 = pw0; fits && p0 < pw1; p0 += 32u) {
+    const uint32_t p = p0 + uint32_t(lane);
+    const int kk = ob + 1 + lane;
+    uint32_t bit = 0;
+    if (kk < int(items)) {
+      const uint32_t v = s_off[kk] - p0;   // >= 0: item ob + 1 starts after position p0 - 1
+      if (v < 32u) bit = 1u << v;
+    }
+    const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
+    const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);   // positions p0 .. p
+    const int owner = ob + __popc(starts & upto);
+    ob = __shfl_sync(0xffffffffu, owner, 31);
+    if (p >= pw1) continue;
+    const uint32_t lo = uint32_t(owner);
     const uint2 r = s_rect[lo];
     const uint32_t x0 = r.x & 0xFFFFu, x1 = r.x >> 16, y0 = r.y & 0xFFFFu, y1 = r.y >> 16;
     const uint32_t tx0 = x0 >> 4, ty0 = y0 >> 4;
