@@ -175,15 +175,22 @@ def cpu_baseline(assets, inst, tau, frame_t=0, inst_frac=0.1, n_pix=16, seed=0):
     return 1.0 / frame_s, t_sel + t_proj + t_pix, desc
 
 
+REF_RUN_S = 180.0   # oracle work of the whole reference run (warm-up and timed steps), seconds
+
+
 def run_reference(args, rank, world):
     """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
     if rank != 0:
         return
     assets, inst = load_scene()
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    # each step samples enough instances for about REF_RUN_S / (warmup + steps) seconds of oracle
+    # work (2% of the instances take about 17 s), so the whole run ends within a few minutes
+    per_step_s = max(1.0, REF_RUN_S / max(1, args.warmup + args.steps))
+    frac = min(0.02, max(1.0 / inst.n, 0.02 * per_step_s / 17.0))
     vals, spent, desc = [], 0.0, ""
     for s in range(args.warmup + args.steps):
-        v, sec, desc = cpu_baseline(assets, inst, args.tau, frame_t=(7 * s) % 300, seed=s, inst_frac=0.02, n_pix=4)
+        v, sec, desc = cpu_baseline(assets, inst, args.tau, frame_t=(7 * s) % 300, seed=s, inst_frac=frac, n_pix=4)
         if s >= args.warmup:
             vals.append(v)
             spent += sec
