@@ -10,9 +10,14 @@
 //
 // In host code the name g_scratch is only a host-side stand-in for the device symbol, not a
 // device address.  The first call on each device (with that device current) resolves the address
-// with cudaGetSymbolAddress and caches it; that first call should come before any stream capture.
+// with cudaGetSymbolAddress and caches it; that first call should come before any stream capture,
+// and the cached address does not survive a device reset (cudaDeviceReset), after which the entry
+// point must not be used in the same process.
 // All calls share the one array and its contents persist between calls: each call clears the
 // words that must start at zero, and calls whose work overlaps on the GPU race with each other.
+// The look-back status words are not cleared per call; each call tags them with fresh epochs
+// from a 64-bit call counter, and the whole status area is cleared whenever the 30-bit epoch
+// sequence starts over, so a stale word from an earlier call never carries a current epoch.
 #include <atomic>
 #include <mutex>
 
@@ -39,7 +44,9 @@ static __device__ __align__(256) unsigned char g_scratch[kBytes];
 
 std::mutex g_mu;
 void* g_base[kMaxDevices] = {};
-std::atomic<uint32_t> g_epoch{1};
+std::atomic<uint64_t> g_calls{0};
+// each call takes 8 consecutive epochs (the sort uses at most 4); the sequence has this period
+constexpr uint64_t kEpochCalls = ((1u << 30) - 16u) / 8u;
 
 __global__ void k_store_n(uint32_t* p, uint32_t v) { *p = v; }
 
@@ -75,8 +82,13 @@ extern "C" v3dg_status v3dg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, u
   sc.status = reinterpret_cast<uint64_t*>(b + kOffStatus);
   sc.max_tiles = kTiles;
   sc.tile_counters = misc + 1;
-  // fresh epochs for the look-back status words, which keep earlier calls' contents
-  uint32_t epoch = (g_epoch.fetch_add(8) % ((1u << 30) - 16u)) + 1u;
+  // fresh epochs for the look-back status words, which keep earlier calls' contents; when the
+  // sequence starts over, clear them so that no word left by an earlier call matches an epoch
+  const uint64_t call = g_calls.fetch_add(1);
+  uint32_t epoch = uint32_t(8u * (call % kEpochCalls)) + 1u;
+  if (call % kEpochCalls == 0 &&
+      cudaMemsetAsync(b + kOffStatus, 0, 8 * size_t(kTiles) * 256, st) != cudaSuccess)
+    return V3DG_ECUDA;
   bool in1 = false;
   int launches = 0;
   uint32_t* tk = reinterpret_cast<uint32_t*>(b + kOffKeys);
