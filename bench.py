@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--instances", type=int, default=N_INST, help="fewer instances: a smaller case for profiling")
     ap.add_argument("--slots", type=int, default=4, help="server slots of the served leg (0: no served leg)")
     ap.add_argument("--serve-requests", type=int, default=150)
-    ap.add_argument("--views", type=int, default=8, help="views per launch of the batched leg (0: none)")
+    ap.add_argument("--views", type=int, default=16, help="views per launch of the batched leg (0: none)")
+    ap.add_argument("--no-extra-legs", action="store_true", help="skip the orbit table and the no-LOD comparison")
     return ap.parse_args()
 
 
@@ -143,64 +144,192 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def cpu_baseline(assets, inst, tau, frame_t=0, inst_frac=0.1, n_pix=16, seed=0):
-    """The FP64 oracle on a bounded sample of one crowd frame, extrapolated to a whole frame.
+# ---------------------------------------------------------------- the oracle on the host cores
+# The FP64 oracle (oracle/) timed on all host cores: a pool of spawned worker processes (no CUDA in
+# them) renders bands of rows of a frame and selects and projects instances in parallel.
 
-    Sample: for a random fraction of the instances, selection, projection of their cut and the
-    per-pixel blend of a few random pixels over those Gaussians; selection and projection scale
-    with 1 / fraction, the blend with the pixel count and 1 / fraction.  Returns frames/s, seconds
-    spent, description.
-    """
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def oracle_pool(cores: int):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(cores)
+
+
+_ASSET = {}
+
+
+def _asset(seed: int, n_leaves: int):
+    """The worker's assets, at most three at a time (each is ~0.5 GB in host memory)."""
+    if (seed, n_leaves) not in _ASSET:
+        from synth.assets import cached_asset
+        while len(_ASSET) >= 3:
+            _ASSET.pop(next(iter(_ASSET)))
+        _ASSET[(seed, n_leaves)] = cached_asset(seed, n_leaves)
+    return _ASSET[(seed, n_leaves)]
+
+
+def _w_band(args):
+    """Worker: a region of a frame by the per-pixel definition."""
+    import oracle
+    p_sub, width, height, region = args
+    return region, oracle.render_image(p_sub, width, height, region=region)
+
+
+def _near_windows(p, windows):
+    """Gaussians whose widened pixel box (the oracle's +-2 px) overlaps one of the windows."""
+    hit = np.zeros(len(p.inst), bool)
+    for x0, y0, x1, y1 in windows:
+        hit |= (p.pix[:, 0] - 2 <= x1) & (p.pix[:, 1] + 2 >= x0) & (p.pix[:, 2] - 2 <= y1) & (p.pix[:, 3] + 2 >= y0)
+    return np.nonzero(hit & p.visible)[0]
+
+
+def _w_instances(args):
+    """Worker: selection and projection of some instances of one asset, each timed on its own
+    (asset loading excluded); returns the times, the visible counts and a random sample of at most
+    `keep` visible Gaussians per instance."""
+    import oracle
+    from synth import scenes
+    seed, n_leaves, ids, inst, cam, tau, keep = args
+    asset = _asset(seed, n_leaves)
+    times, n_vis, parts = [], [], []
+    for k, i in enumerate(ids):
+        one = scenes.subset(inst, [k])
+        one.asset[:] = 0
+        t0 = time.perf_counter()
+        cut = oracle.select([asset], one, cam, tau)
+        p = oracle.project([asset], one, cam, cut)
+        times.append(time.perf_counter() - t0)
+        vis = np.nonzero(p.visible)[0]
+        n_vis.append(len(vis))
+        pick = np.random.default_rng(i).choice(vis, size=min(keep, len(vis)), replace=False) if len(vis) else vis
+        sub = oracle.subset_projected(p, np.sort(pick))
+        sub.inst[:] = i
+        parts.append(sub)
+    return times, n_vis, parts
+
+
+def _render_frame_parallel(pool, p, width, height, band=16):
+    import oracle
+    tasks = []
+    for y0 in range(0, height, band):
+        y1 = min(y0 + band - 1, height - 1)
+        idx = _near_windows(p, [(0, y0, width - 1, y1)])
+        tasks.append((oracle.subset_projected(p, idx), width, height, (0, y0, width - 1, y1)))
+    C = np.zeros((height, width, 3))
+    for (x0, y0, x1, y1), (c, _, _) in pool.imap_unordered(_w_band, tasks):
+        C[y0:y1 + 1] = c
+    return C
+
+
+def oracle_config1(pool, frames: int = 2):
+    """Config 1 (100k leaves, 256x256, fov 60, distance 3, tau 1 px), whole frames measured end
+    to end: selection and projection, then the image in bands of 16 rows over the pool."""
+    import oracle
+    from synth import scenes
+    from synth.assets import cached_asset
+    asset = cached_asset(0, 100_000)
+    inst = scenes.single_instance()
+    cam = scenes.tiny_camera()
+    t0 = time.perf_counter()
+    for _ in range(frames):
+        cut = oracle.select([asset], inst, cam, 1.0)
+        p = oracle.project([asset], inst, cam, cut)
+        _render_frame_parallel(pool, p, cam.width, cam.height)
+    dt = time.perf_counter() - t0
+    return frames / dt, dt
+
+
+def oracle_crowd_sample(pool, cores, assets_n, inst, tau, frame_t, n_sample, seed, n_leaves=N_LEAVES, keep=2000):
+    """One crowd frame estimated from a sample.  n_sample random instances are selected and
+    projected on the pool (each timed by its worker); then a random sample of their visible
+    Gaussians is rendered over the whole frame by the per-pixel definition (Gaussian by Gaussian,
+    whose cost grows with the number of Gaussians).  Selection and projection scale with the
+    instances, the image with the visible Gaussians, and both divide over the cores: an
+    extrapolation.  Returns (frames/s, wall s, description)."""
     import oracle
     from synth import scenes
     cam = scenes.crowd_camera(frame_t)
     rng = np.random.default_rng(seed)
-    pick = np.sort(rng.choice(inst.n, size=max(1, int(round(inst.n * inst_frac))), replace=False))
-    sub_inst = scenes.subset(inst, pick)
+    pick = np.sort(rng.choice(inst.n, size=min(n_sample, inst.n), replace=False))
+    tasks = []
+    for a in range(assets_n):
+        ids = pick[inst.asset[pick] == a]
+        for chunk in np.array_split(ids, max(1, min(len(ids), 2))):
+            if len(chunk):
+                tasks.append((a, n_leaves, chunk.tolist(), scenes.subset(inst, chunk), cam, tau, keep))
     t0 = time.perf_counter()
-    cut = oracle.select(assets, sub_inst, cam, tau)
-    t_sel = time.perf_counter() - t0
+    times, n_vis, parts = [], [], []
+    for tt, nv, pp in pool.imap_unordered(_w_instances, tasks):
+        times += tt
+        n_vis += nv
+        parts += pp
+    t_par = time.perf_counter() - t0
+    fields = oracle.Projected.__dataclass_fields__
+    p = oracle.Projected(**{k: np.concatenate([getattr(q, k) for q in parts]) for k in fields})
     t1 = time.perf_counter()
-    proj = oracle.project(assets, sub_inst, cam, cut)
-    t_proj = time.perf_counter() - t1
-    pix = [(int(rng.integers(0, WIDTH)), int(rng.integers(0, HEIGHT))) for _ in range(n_pix)]
-    t2 = time.perf_counter()
-    oracle.render_pixels(proj, pix)
-    t_pix = time.perf_counter() - t2
+    oracle.render_image(p, WIDTH, HEIGHT)
+    t_img = time.perf_counter() - t1
     scale = inst.n / len(pick)
-    frame_s = (t_sel + t_proj) * scale + t_pix * scale * (WIDTH * HEIGHT / n_pix)
-    desc = (f"walk frame {frame_t}, {len(pick)} random instances of {inst.n}: select ({t_sel:.2f} s) and project "
-            f"their cut ({t_proj:.2f} s), both x{scale:.0f}; blend {n_pix} random pixels ({t_pix:.2f} s, "
-            f"x{WIDTH * HEIGHT / n_pix * scale:.3g}); whole frame extrapolated to {frame_s:.0f} s")
-    return 1.0 / frame_s, t_sel + t_proj + t_pix, desc
+    per_g = t_img / max(1, len(p.inst))
+    frame_s = (sum(times) * scale + per_g * sum(n_vis) * scale) / cores
+    desc = (f"walk frame {frame_t}: {len(pick)} random instances of {inst.n} selected and projected on the pool "
+            f"({sum(times):.1f} CPU-s, x{scale:.0f}); {len(p.inst)} of their {sum(n_vis)} visible Gaussians "
+            f"rendered over the whole frame ({t_img:.2f} s, {per_g * 1e6:.0f} us per Gaussian, x{sum(n_vis) * scale:.3g} "
+            f"Gaussians); extrapolated to {frame_s:.0f} s per frame on {cores} cores")
+    return 1.0 / frame_s, t_par + t_img, desc
 
 
-REF_RUN_S = 180.0   # oracle work of the whole reference run (warm-up and timed steps), seconds
+def cpu_baseline_leg(assets_n, inst, tau):
+    """The oracle on all host cores: config 1 whole frames (measured) and the crowd walk frames
+    0, 150, 299 (extrapolated from samples)."""
+    cores = host_cores()
+    with oracle_pool(cores) as pool:
+        c1_fps, c1_s = oracle_config1(pool)
+        vals, spent, descs = [], 0.0, []
+        for t in (0, 150, 299):
+            v, sec, d = oracle_crowd_sample(pool, cores, assets_n, inst, tau, t, n_sample=cores, seed=t)
+            vals.append(v)
+            spent += sec
+            descs.append(d)
+    return {"value": float(np.mean(vals)), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "extrapolated": True,
+            "sample": "; ".join(descs) + f" ({spent:.0f} s wall)",
+            "config1_measured": {"value": c1_fps, "unit": "frames/s", "frames": 2, "seconds": c1_s,
+                                 "workload": "config 1: 100k leaves, 256x256, fov 60, distance 3, tau 1 px, "
+                                             "whole frames (selection, projection, image in 16-row bands on the pool)"}}
+
+
+REF_RUN_S = 150.0   # wall time of the whole reference run (warm-up and timed steps), seconds
 
 
 def run_reference(args, rank, world):
-    """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    """The reference arm: the FP64 oracle on all host cores (rank 0 only), one crowd walk frame
+    per step, each extrapolated from a sample of instances and pixels sized from the step count."""
     if rank != 0:
         return
     assets, inst = load_scene()
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    # each step samples enough instances for about REF_RUN_S / (warmup + steps) seconds of oracle
-    # work (2% of the instances take about 17 s), so the whole run ends within a few minutes
-    per_step_s = max(1.0, REF_RUN_S / max(1, args.warmup + args.steps))
-    frac = min(0.02, max(1.0 / inst.n, 0.02 * per_step_s / 17.0))
+    cores = host_cores()
+    steps = max(1, args.warmup + args.steps)
+    # about 1 s of wall time per sampled instance per core (selection and projection on the Grace
+    # host), so the whole run stays near REF_RUN_S
+    n_sample = int(min(4 * cores, max(cores // 2, REF_RUN_S / steps * cores / 2)))
     vals, spent, desc = [], 0.0, ""
-    for s in range(args.warmup + args.steps):
-        v, sec, desc = cpu_baseline(assets, inst, args.tau, frame_t=(7 * s) % 300, seed=s, inst_frac=frac, n_pix=4)
-        if s >= args.warmup:
-            vals.append(v)
-            spent += sec
+    with oracle_pool(cores) as pool:
+        for s in range(steps):
+            v, sec, desc = oracle_crowd_sample(pool, cores, len(assets), inst, args.tau, (7 * s) % 300, n_sample, s)
+            if s >= args.warmup:
+                vals.append(v)
+                spent += sec
     fps = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / fps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "tau_px": args.tau},
-            "cpu_baseline": {"kind": "oracle", "value": fps, "unit": "frames/s", "cores": 1,
-                             "sample": "per step: " + desc + f"; host has {cores} cores, numpy runs on 1"},
+            "cpu_baseline": {"kind": "oracle", "value": fps, "unit": "frames/s", "cores": cores, "extrapolated": True,
+                             "sample": "per step: " + desc},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -325,7 +454,7 @@ def main():
     h2d = inst.n * 256
     d2h = WIDTH * HEIGHT * 3 * 4
 
-    served = None
+    served, view_samples = None, []
     if args.slots > 0:
         # the autotuner times the blend of one FP16 walk frame with every batch size and split
         ctx.set_instances(inst16)
@@ -334,11 +463,18 @@ def main():
         tuned = ctx.autotune_blend()
         ctx.set_instances(inst)
         served = serve_leg(ctx, inst, inst16, cams, timed_ids, args.tau, args.slots, args.serve_requests,
-                           {"batch": tuned["batch"], "split_pairs": tuned["split_pairs"]})
+                           {"mode": tuned["mode"], "batch": tuned["batch"], "split_pairs": tuned["split_pairs"]})
         served["autotune"] = tuned
         served["psnr_fp16_vs_fp32_db"] = fp16_psnr(ctx, inst, inst16, cams, timed_ids, args.tau)
         if args.views > 0:
-            served["batched"] = batched_leg(ctx, inst, inst16, cams, timed_ids, args.tau, args.views, tuned)
+            served["batched"], view_samples = batched_leg(ctx, inst, inst16, cams, timed_ids, (1.0, 2.0), args.views,
+                                                          tuned)
+
+    extra = {}
+    if not args.no_extra_legs:
+        extra["vanilla"] = vanilla_leg(ctx, inst, cams, timed_ids, args.tau)
+        extra["orbit"] = orbit_leg(ctx, 0)
+        ctx.set_instances(inst)
 
     peaks, peak_kind = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
@@ -348,9 +484,9 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            v, spent, desc = cpu_baseline(assets, inst, args.tau, inst_frac=0.02, n_pix=16)
-            cpu = {"value": v, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                   "sample": desc + f" ({spent:.0f} s of CPU work, single-threaded numpy)"}
+            cpu = cpu_baseline_leg(len(assets), inst, args.tau)
+            if view_samples:
+                served["batched"]["per_view_vs_oracle"] = oracle_view_parity(view_samples, assets, inst)
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -363,6 +499,8 @@ def main():
             "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "served": served,
+            "v3dg_vs_vanilla": extra.get("vanilla"),
+            "orbit": extra.get("orbit"),
             "gpu_launches": int(launches),
             "stages_ms": stage_ms,
             "select_flat_ms": float(np.mean(flat_select)),
@@ -427,11 +565,12 @@ def _pcts(lat):
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
 
 
-DEFAULT_BLEND = {"batch": 512, "split_pairs": 0xFFFFFFFF}
+DEFAULT_BLEND = {"mode": 0, "batch": 512, "split_pairs": 0xFFFFFFFF}
 
 
 def _blend_options(ctx, opts):
     from paper_2505_06523_gb300 import _native as N
+    ctx.set_option(N.V3DG_OPT_BLEND_MODE, opts["mode"])
     ctx.set_option(N.V3DG_OPT_BLEND_BATCH, opts["batch"])
     ctx.set_option(N.V3DG_OPT_SPLIT_PAIRS, opts["split_pairs"])
 
@@ -479,56 +618,184 @@ def serve_leg(ctx, inst, inst16, cams, frame_ids, tau, slots, n_req, tuned):
     return out
 
 
-def batched_leg(ctx, inst, inst16, cams, frame_ids, tau, views, tuned):
-    """Frames in batches: `views` consecutive walk frames per v3dg_select_views + v3dg_render
-    (every stage one launch for all of them), replayed as a CUDA graph, FP16 colour, autotuned
-    blend; device images.  frames/s = views x batches / time (CUDA events), beside the same frames
-    one at a time with the same options."""
+def batched_leg(ctx, inst, inst16, cams, frame_ids, taus, views, tuned, n_groups=3):
+    """Config 4: `views` consecutive walk frames per v3dg_select_views + v3dg_render (every stage one
+    launch for all of them), replayed as a CUDA graph, FP16 colour, autotuned blend, device images,
+    for each tau.  frames/s = views x batches / time (CUDA events), beside the same frames one at a
+    time with the same options.  Per view: PSNR of the FP16 image against the FP32 one (device), and
+    pixel samples of both (two 8x8 windows) that the oracle leg compares with the FP64 oracle."""
     import torch
     from paper_2505_06523_gb300 import _native as N
-    _blend_options(ctx, tuned)
-    ctx.set_instances(inst16)
-    ctx.set_option(N.V3DG_OPT_GRAPHS, 1)
-    groups = [[cams[(f + v) % len(cams)] for v in range(views)] for f in frame_ids[:6]]
-    out = torch.empty((views, HEIGHT, WIDTH, 3), dtype=torch.float32, device="cuda")
-    for g in groups[:2]:   # buffers grow, the graph is captured
-        ctx.select_views(g, tau)
-        ctx.render(out)
-    ctx.set_option(N.V3DG_OPT_SYNC_CHECK, 0)
+    out = {"views_per_launch": views, "path": "FP16 colour, autotuned blend, CUDA graph", "taus": {}}
+    samples = []
+    for tau in taus:
+        _blend_options(ctx, tuned)
+        ctx.set_instances(inst16)
+        ctx.set_option(N.V3DG_OPT_GRAPHS, 1)
+        groups = [[(f + v) % len(cams) for v in range(views)] for f in frame_ids[:n_groups]]
+        img = torch.empty((views, HEIGHT, WIDTH, 3), dtype=torch.float32, device="cuda")
+        for g in groups[:2]:   # buffers grow, the graph is captured
+            ctx.select_views([cams[f] for f in g], tau)
+            ctx.render(img)
+        ctx.set_option(N.V3DG_OPT_SYNC_CHECK, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        for g in groups:
+            ctx.select_views([cams[f] for f in g], tau)
+            ctx.render(img)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        batched_ms = e0.elapsed_time(e1)
+        st = ctx.frame_stats()
+        one = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32, device="cuda")
+        for f in groups[0]:
+            ctx.select(cams[f], tau)
+            ctx.render(one)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        for g in groups:
+            for f in g:
+                ctx.select(cams[f], tau)
+                ctx.render(one)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        single_ms = e0.elapsed_time(e1)
+        ctx.set_option(N.V3DG_OPT_SYNC_CHECK, 1)
+        ctx.set_option(N.V3DG_OPT_GRAPHS, 0)
+        if st["overflow"] or st["timeout"]:
+            raise RuntimeError(f"a batched frame was invalid: {st}")
+        # per view of the last batch: FP16 (the batched image) against FP32 (plain, one at a time)
+        g = groups[-1]
+        ctx.set_instances(inst)
+        _blend_options(ctx, DEFAULT_BLEND)
+        psnr, maxabs = [], []
+        rng = np.random.default_rng(int(tau * 100))
+        for v, f in enumerate(g):
+            ctx.select(cams[f], tau)
+            ref = ctx.render(one)[0]
+            d = (img[v].double() - ref.double())
+            mse = float((d ** 2).mean())
+            psnr.append(float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse))
+            maxabs.append(float(d.abs().max()))
+            if v in (0, views - 1):
+                drawn = torch.nonzero(ref.amax(dim=-1) > 0.05).cpu().numpy()
+                wins = []
+                for y, x in drawn[rng.choice(len(drawn), size=2, replace=False)]:
+                    x0, y0 = int(min(max(x - 4, 0), WIDTH - 8)), int(min(max(y - 4, 0), HEIGHT - 8))
+                    wins.append((x0, y0, x0 + 7, y0 + 7))
+                pix = [(x, y) for x0, y0, x1, y1 in wins for y in range(y0, y1 + 1) for x in range(x0, x1 + 1)]
+                i16, i32 = img[v].cpu().numpy(), ref.cpu().numpy()
+                samples.append({"tau": tau, "view": v, "frame": f, "windows": wins, "pixels": pix,
+                                "fp16": np.array([i16[y, x] for x, y in pix]),
+                                "fp32": np.array([i32[y, x] for x, y in pix])})
+        n = views * len(groups)
+        out["taus"][f"{tau:g}"] = {"frames": n, "value": n / (batched_ms / 1000.0), "unit": "frames/s",
+                                   "same_frames_one_at_a_time": n / (single_ms / 1000.0),
+                                   "pairs_last_batch": st["pairs"], "visible_last_batch": st["visible"],
+                                   "psnr_fp16_vs_fp32_db": psnr, "maxabs_fp16_vs_fp32": maxabs}
+        del img
+        torch.cuda.synchronize()
+    ctx.set_instances(inst)
+    _blend_options(ctx, DEFAULT_BLEND)
+    return out, samples
+
+
+def oracle_view_parity(samples, assets, inst):
+    """Part of the oracle leg: the sampled pixels of the batched views against the FP64 oracle,
+    on the FP32 attributes and on the FP16-rounded ones (what the FP16 path stores).  Per sample:
+    PSNR and max abs error over the pixels outside the decision bands, for the FP16 image and for
+    the plain FP32 image of the same frame."""
+    import copy
+    import oracle
+    from synth import scenes
+
+    def rounded(a):
+        b = copy.copy(a)
+        b.sh = a.sh.astype(np.float16).astype(np.float32)
+        b.opacity = a.opacity.astype(np.float16).astype(np.float32)
+        return b
+
+    a16 = [rounded(a) for a in assets]
+    rows = []
+    for smp in samples:
+        cam = scenes.crowd_camera(smp["frame"])
+        row = {"tau": smp["tau"], "view": smp["view"], "frame": smp["frame"], "pixels": len(smp["pixels"])}
+        for attrs, name in ((assets, "oracle_fp32_attrs"), (a16, "oracle_fp16_attrs")):
+            cut = oracle.select(attrs, inst, cam, smp["tau"])
+            sub, only = oracle.gaussians_reaching_pixels(attrs, inst, cam, cut, smp["pixels"], windows=smp["windows"])
+            p = oracle.project(attrs, inst, cam, sub, only=only)
+            c, _, b = oracle.render_pixels(p, smp["pixels"])
+            for img in ("fp16", "fp32"):
+                g = smp[img].astype(np.float64)
+                mse = float(np.mean((g - c) ** 2))
+                row[f"{img}_image_vs_{name}"] = {
+                    "psnr_db": float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse),
+                    "maxabs_outside_bands": float(np.abs(g - c).max(axis=1)[~b].max()) if (~b).any() else 0.0,
+                    "band_pixels": int(b.sum())}
+        rows.append(row)
+    return rows
+
+
+def _frame_ms(ctx, cams, tau, rgb, reps=1):
+    """Mean device time (CUDA events on the library's stream) of select + render over the cameras,
+    after one checked warm-up pass over them (buffers grown); also the last frame's counters."""
+    import torch
+    for cam in cams:
+        ctx.select(cam, tau)
+        ctx.render(rgb)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(ctx.stream)
-    for g in groups:
-        ctx.select_views(g, tau)
-        ctx.render(out)
+    for _ in range(reps):
+        for cam in cams:
+            ctx.select(cam, tau)
+            ctx.render(rgb)
     e1.record(ctx.stream)
     torch.cuda.synchronize()
-    batched_ms = e0.elapsed_time(e1)
-    st = ctx.frame_stats()
-    one = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32, device="cuda")
-    for g in groups[:1]:
-        for cam in g:
-            ctx.select(cam, tau)
-            ctx.render(one)
-    torch.cuda.synchronize()
-    e0.record(ctx.stream)
-    for g in groups:
-        for cam in g:
-            ctx.select(cam, tau)
-            ctx.render(one)
-    e1.record(ctx.stream)
-    torch.cuda.synchronize()
-    single_ms = e0.elapsed_time(e1)
-    ctx.set_option(N.V3DG_OPT_SYNC_CHECK, 1)
-    ctx.set_option(N.V3DG_OPT_GRAPHS, 0)
+    return e0.elapsed_time(e1) / (reps * len(cams)), ctx.frame_stats()
+
+
+def orbit_leg(ctx, asset_id):
+    """Config 2: one 1M-leaf asset at 1920x1080, fov 45, elevation 30, eight orbit distances
+    1.5 (50 / 1.5)^(k / 7), tau in {0.5, 1, 2, 4} px and tau = 0 (every leaf: the scene without
+    LOD).  Per (distance, tau): cut clusters, selected and rendered (visible) Gaussians, pairs and
+    the frame's device time."""
+    import torch
+    from synth import scenes
+    one = scenes.single_instance()
+    one.asset[:] = asset_id
+    ctx.set_instances(one)
+    rgb = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32, device="cuda")
+    rows = []
+    for k, d in enumerate(scenes.orbit_distances()):
+        cam = scenes.orbit_camera(d)
+        row = {"k": k, "distance": d}
+        for tau in (0.0, 0.5, 1.0, 2.0, 4.0):
+            ms, st = _frame_ms(ctx, [cam], tau, rgb, reps=5)
+            row[f"tau{tau:g}"] = {"ms": ms, "cut_nodes": st["cut_nodes"], "selected": st["cut_gaussians"],
+                                  "rendered": st["visible"], "pairs": st["pairs"]}
+        row["speedup_tau1_vs_tau0"] = row["tau0"]["ms"] / row["tau1"]["ms"]
+        rows.append(row)
+    return {"workload": "asset 0 (1M leaves), 1920x1080, fov 45, elevation 30, 8 distances, tau 0 (no LOD) and "
+                        "0.5-4 px; ms = device time of select + render, mean of 5 frames", "rows": rows}
+
+
+def vanilla_leg(ctx, inst, cams, frame_ids, tau):
+    """The crowd with V3DG's cut against the same scene without LOD (tau = 0: every leaf cluster is
+    selected), on the same walk frames: the paper's speed-up comparison (Sec. 5.3)."""
+    import torch
+    rgb = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32, device="cuda")
     ctx.set_instances(inst)
-    _blend_options(ctx, DEFAULT_BLEND)
-    if st["overflow"] or st["timeout"]:
-        raise RuntimeError(f"a batched frame was invalid: {st}")
-    n = views * len(groups)
-    return {"views_per_launch": views, "frames": n, "path": "FP16 colour, autotuned blend, CUDA graph",
-            "value": n / (batched_ms / 1000.0), "unit": "frames/s",
-            "same_frames_one_at_a_time": n / (single_ms / 1000.0)}
+    sel = [cams[f] for f in frame_ids[:8]]
+    out = {}
+    for name, t in (("v3dg", tau), ("vanilla", 0.0)):
+        ms, st = _frame_ms(ctx, sel, t, rgb)
+        out[name] = {"tau_px": t, "ms": ms, "frames_per_s": 1000.0 / ms, "selected_last": st["cut_gaussians"],
+                     "rendered_last": st["visible"], "pairs_last": st["pairs"]}
+    out["speedup"] = out["vanilla"]["ms"] / out["v3dg"]["ms"]
+    out["frames"] = len(sel)
+    return out
 
 
 def fp16_psnr(ctx, inst, inst16, cams, frame_ids, tau):

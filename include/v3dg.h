@@ -100,6 +100,8 @@ typedef struct {
   uint64_t blend_evals;     /* (pixel, Gaussian) pairs the blend evaluated inside the Gaussian's
                                pixel box (only with V3DG_OPT_COUNT_WORK, else 0) */
   uint64_t blend_contribs;  /* of those, the ones with alpha >= 1/255 that were blended */
+  uint64_t conic_fp64;      /* Gaussians whose 2D covariance had det < 1e-12 (eps2d = 0, Sec. 5.1, lets
+                               it approach 0) and was formed and inverted in FP64 */
 } v3dg_stats;
 
 /* Options for v3dg_set_option. */
@@ -126,6 +128,14 @@ enum {
                                 more than 8M tests, else flat. */
   V3DG_OPT_BLEND_BATCH = 9,    /* records the blend stages per batch in shared memory: 128, 256
                                 or 512 (default); the image does not depend on it */
+  V3DG_OPT_BLEND_MODE = 11,    /* blend kernel variant, the same image bit for bit: 0 (default)
+                                two phases per batch, a record-parallel alpha test into per-pixel
+                                masks, then pixel-parallel compositing; 1: each batch staged into
+                                shared memory by bulk copies (cp.async.bulk, one per 48-byte record,
+                                completing on an mbarrier with a bounded wait), then composited by
+                                warps that each own two pixel rows and walk only the records whose
+                                box spans them.  Variant 1 always blends whole tiles
+                                (V3DG_OPT_SPLIT_PAIRS is ignored). */
   V3DG_OPT_GRAPHS = 10         /* 1: v3dg_select only stages the camera and instances, and
                                 v3dg_render runs the selection and the whole render as one CUDA
                                 graph, captured the first time a configuration (instance and view
@@ -184,15 +194,16 @@ v3dg_status v3dg_select_views(v3dg_ctx* ctx, const v3dg_camera* cams, uint32_t n
  * (V3DG_ENOTFOUND otherwise). */
 v3dg_status v3dg_render(v3dg_ctx* ctx, float* rgb_out, float* T_out);
 
-/* Autotuner of the blend's batch size and work split.  Re-runs the blend stage of the last
- * rendered frame (its sorted pairs and records are still on the device) with every combination of
- * records per batch (128, 256, 512) and long-tile split threshold (4096, 16384, 65536 pairs, or
- * none), times each with CUDA events (best of 3 after one warm-up run) and keeps the fastest as
- * V3DG_OPT_BLEND_BATCH and V3DG_OPT_SPLIT_PAIRS for the frames that follow.  Neither changes the
+/* Autotuner of the blend's kernel variant, batch size and work split.  Re-runs the blend stage of
+ * the last rendered frame (its sorted pairs and records are still on the device) with every
+ * combination of variant (V3DG_OPT_BLEND_MODE 0, 1), records per batch (128, 256, 512) and, for
+ * variant 0, long-tile split threshold (4096, 16384, 65536 pairs, or none), times each with CUDA
+ * events (best of 3 after one warm-up run) and keeps the fastest as V3DG_OPT_BLEND_MODE,
+ * V3DG_OPT_BLEND_BATCH and V3DG_OPT_SPLIT_PAIRS for the frames that follow.  None changes the
  * image.  Synchronous; the caller's image is not touched.  V3DG_ENOTFOUND without a rendered
- * frame, V3DG_EOVERFLOW if that frame was not valid.  batch, split_pairs, best_ms: the choice and
- * its time, each may be NULL.  The paper has no counterpart (its rasterizer is fixed). */
-v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* batch, uint32_t* split_pairs, float* best_ms);
+ * frame, V3DG_EOVERFLOW if that frame was not valid.  mode, batch, split_pairs, best_ms: the choice
+ * and its time, each may be NULL.  The paper has no counterpart (its rasterizer is fixed). */
+v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* mode, uint32_t* batch, uint32_t* split_pairs, float* best_ms);
 
 /* v3dg_render into HOST buffers (same layouts): the image is produced on the device and copied
  * back before the call returns. */
@@ -230,6 +241,18 @@ v3dg_status v3dg_stage_times(v3dg_ctx* ctx, float* ms, int n, uint64_t* launches
 v3dg_status v3dg_sort_pairs(v3dg_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t n,
                             int begin_bit, int end_bit);
 
+/* Diagnostic of the bounded device-side waits (the paper has no counterpart).  Every chained scan
+ * of the path (selection compaction, pair expansion, radix-sort passes) finds its offsets with a
+ * decoupled look-back that polls earlier tiles' status words at most a fixed number of times and
+ * then gives up, flags the frame (V3DG_ETIMEOUT) and returns, so that a wait can never hang the
+ * GPU.  This call runs both look-back variants (the sort's, one thread with several words per
+ * round, and the warp-wide one) as tile 1 of a two-tile chain, with at most spin_limit polls
+ * (1 .. 2^20).  predecessor_publishes != 0: tile 0 publishes its prefix first; the call returns
+ * V3DG_OK and *prefix (may be NULL) receives the prefix found (1000).  0: tile 0 never publishes;
+ * the waits give up after spin_limit polls, the kernel returns, and the call reports
+ * V3DG_ETIMEOUT.  Synchronous on the context's stream; the context stays usable either way. */
+v3dg_status v3dg_check_wait(v3dg_ctx* ctx, uint32_t spin_limit, int predecessor_publishes, uint32_t* prefix);
+
 /* Largest n that v3dg_sort_pairs_noalloc accepts (its fixed scratch holds this many pairs). */
 #define V3DG_SORT_NOALLOC_MAX_PAIRS (1u << 20)
 
@@ -244,8 +267,10 @@ v3dg_status v3dg_sort_pairs(v3dg_ctx* ctx, uint32_t* keys, uint32_t* vals, uint6
  *  - n > V3DG_SORT_NOALLOC_MAX_PAIRS returns V3DG_EOVERFLOW and does nothing; bad pointers or
  *    bit ranges return V3DG_EINVAL; a bounded device wait that gave up returns V3DG_ETIMEOUT.
  *  - Synchronises cuda_stream before returning.  The first call on a device looks up the scratch
- *    array's address (make it before any stream capture).  All calls share the one array: calls
- *    whose work overlaps on the GPU race with each other. */
+ *    array's address and keeps it; make that first call before any stream capture.  The kept
+ *    address does not survive cudaDeviceReset: after a device reset the entry point must not be
+ *    used again in the same process.  All calls share the one array: calls whose work overlaps on
+ *    the GPU race with each other. */
 v3dg_status v3dg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, uint64_t n, int begin_bit, int end_bit,
                                     void* cuda_stream);
 

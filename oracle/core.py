@@ -44,11 +44,14 @@ ALPHA_MIN = 1.0 / 255.0
 T_STOP = 1e-4
 CLAMP_FOV = 1.3          # EWA Jacobian evaluated at the mean clamped to 1.3x the half-fov
 
-# decision bands that separate rounding noise from real disagreements (see the tests)
+# Decision bands that separate rounding noise from real disagreements.  A float32 evaluation can
+# take the other side of a threshold only when the exact value lies within its rounding error of
+# it: the skip (alpha >= 1/255) and stop (T (1 - alpha) >= 1e-4) rules of the blend, the footprint
+# test of the cut, and the pixel-centre test of a Gaussian's tile rectangle.
 TIE_REL = 1e-6           # footprint within this relative distance of tau_F: near tie
-ALPHA_BAND = 1e-3        # alpha within this relative distance of 1/255: boundary pixel
-T_BAND = 2e-3            # T (1 - alpha) within this relative distance of 1e-4: boundary pixel
-EDGE_BAND_PX = 2e-3      # pixel-rectangle edge this close to a tile-changing edge: boundary
+ALPHA_BAND = 1e-5        # alpha within this relative distance of 1/255: boundary pixel
+T_BAND = 1e-5            # T (1 - alpha) within this relative distance of 1e-4: boundary pixel
+EDGE_BAND_PX = 5e-4      # pixel-rectangle edge this close to a tile-changing edge: boundary
 
 
 # ----------------------------------------------------------------------------- transforms
@@ -450,7 +453,21 @@ def node_mean_balls(asset):
     return centre, radius, sigma
 
 
-def nodes_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float = 1.0) -> Cut:
+def _near_any(ux, uy, dx, dy, pixels, windows):
+    """Whether some listed pixel centre (px + 0.5, py + 0.5) lies within (dx, dy) of (ux, uy), or,
+    with ``windows`` ((x0, y0, x1, y1) inclusive pixel rectangles), whether the box around (ux, uy)
+    overlaps a window's span of pixel centres (a superset of the per-pixel test)."""
+    hit = np.zeros(np.shape(ux), bool)
+    if windows is not None:
+        for x0, y0, x1, y1 in windows:
+            hit |= (ux + dx >= x0 + 0.5) & (ux - dx <= x1 + 0.5) & (uy + dy >= y0 + 0.5) & (uy - dy <= y1 + 0.5)
+        return hit
+    for qx, qy in np.asarray([(px + 0.5, py + 0.5) for px, py in pixels], np.float64).reshape(-1, 2):
+        hit |= (np.abs(qx - ux) <= dx) & (np.abs(qy - uy) <= dy)
+    return hit
+
+
+def nodes_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float = 1.0, windows=None) -> Cut:
     """The nodes of the cut whose Gaussians can have alpha >= 1/255 at one of the pixels.
 
     A conservative screen bound per (instance, node), so that the per-pixel definition at a
@@ -464,7 +481,8 @@ def nodes_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float =
         (q <= 2 ln(255 o) <= 2 ln 255) lies within sqrt(2 ln 255) ||J||_2 s sigma of the mean.
     Nodes with z_min <= near are kept unless the whole ball lies behind the near plane (then the
     projection culls all of their Gaussians).  The bound is widened by 2 px (the margin of
-    render_pixels) plus ``slack_px``.
+    render_pixels) plus ``slack_px``.  ``windows``: rectangles of pixels tested as wholes (keeps
+    a superset of the nodes that the pixels inside them would keep).
     """
     m_all = compose(cam.world_to_cam, inst.rot, inst.trans, inst.scale)
     fx, fy, cx, cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
@@ -472,7 +490,6 @@ def nodes_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float =
     limy = CLAMP_FOV * (0.5 * cam.height / fy)
     jn = math.sqrt(fx * fx * (1.0 + limx * limx) + fy * fy * (1.0 + limy * limy))
     ksig = math.sqrt(2.0 * math.log(255.0))
-    q = np.asarray([(px + 0.5, py + 0.5) for px, py in pixels], np.float64).reshape(-1, 2)
     balls = {}
     keep = np.zeros(len(cut.inst), bool)
     by_inst = np.argsort(cut.inst, kind="stable")
@@ -498,30 +515,28 @@ def nodes_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float =
             dx = fx * rv * np.sqrt(cv[:, 0] ** 2 + cv[:, 2] ** 2) / (cv[:, 2] * zmin) + spread
             dy = fy * rv * np.sqrt(cv[:, 1] ** 2 + cv[:, 2] ** 2) / (cv[:, 2] * zmin) + spread
         behind = cv[:, 2] + rv < float(cam.near)   # every mean behind the near plane: all culled
-        hit = ~front & ~behind
-        for qx, qy in q:
-            hit |= front & (np.abs(qx - ux) <= dx) & (np.abs(qy - uy) <= dy)
+        hit = (~front & ~behind) | (front & _near_any(ux, uy, dx, dy, pixels, windows))
         keep[sel] = hit
     return Cut(cut.inst[keep], cut.node[keep], cut.ties)
 
 
-def gaussians_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float = 1.0):
+def gaussians_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: float = 1.0, windows=None):
     """The Gaussians of the cut that can have alpha >= 1/255 at one of the pixels.
 
     First the clusters (nodes_reaching_pixels), then each of their Gaussians by its own bound:
     with its mean at view depth z > near and pixel position u, its alpha >= 1/255 ellipse lies
     within sqrt(2 ln 255) ||J||_2 s sigma of u, ||J||_2 <= sqrt(f_x^2 (1 + l_x^2) + f_y^2
     (1 + l_y^2)) / z and sigma = exp(its largest log-scale).  Gaussians with z <= near are kept.
+    ``windows`` as in nodes_reaching_pixels.
     Returns (the sub-cut of those clusters, {instance: sorted asset-local indices}) for project.
     """
-    sub = nodes_reaching_pixels(assets, inst, cam, cut, pixels, slack_px)
+    sub = nodes_reaching_pixels(assets, inst, cam, cut, pixels, slack_px, windows)
     m_all = compose(cam.world_to_cam, inst.rot, inst.trans, inst.scale)
     fx, fy, cx, cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     limx = CLAMP_FOV * (0.5 * cam.width / fx)
     limy = CLAMP_FOV * (0.5 * cam.height / fy)
     jn = math.sqrt(fx * fx * (1.0 + limx * limx) + fy * fy * (1.0 + limy * limy))
     ksig = math.sqrt(2.0 * math.log(255.0))
-    q = np.asarray([(px + 0.5, py + 0.5) for px, py in pixels], np.float64).reshape(-1, 2)
     only = {}
     by_inst = np.argsort(sub.inst, kind="stable")
     inst_sorted = sub.inst[by_inst]
@@ -542,30 +557,32 @@ def gaussians_reaching_pixels(assets, inst, cam, cut: Cut, pixels, slack_px: flo
             u = fx * view[:, 0] / z + cx
             v = fy * view[:, 1] / z + cy
             spread = ksig * jn * s * sigma / z + 2.0 + slack_px
-        hit = ~front
-        for qx, qy in q:
-            hit |= front & (np.abs(qx - u) <= spread) & (np.abs(qy - v) <= spread)
+        hit = ~front | (front & _near_any(u, v, spread, spread, pixels, windows))
         if hit.any():
             only[int(i)] = local[hit]
     return sub, only
 
 
-def render_image(p: Projected, width: int, height: int):
+def render_image(p: Projected, width: int, height: int, region=None):
     """Whole image by the per-pixel definition, processed Gaussian by Gaussian.
 
     Pixels are updated in blend order; a pixel stops once its stop rule fires.  Only the
     Gaussian's pixel rectangle (where alpha >= 1/255 can hold) is visited, widened by 2 px so
-    that near-threshold pixels are still checked and flagged.
-    Returns (C (h, w, 3), T (h, w), boundary (h, w)).
+    that near-threshold pixels are still checked and flagged.  ``region`` (x0, y0, x1, y1),
+    inclusive: only those pixels are computed (every pixel depends only on its own Gaussians, so
+    regions stitch into the whole image exactly).
+    Returns (C (h, w, 3), T (h, w), boundary (h, w)) of the image or of the region.
     """
-    C = np.zeros((height, width, 3))
-    T = np.ones((height, width))
-    done = np.zeros((height, width), bool)
-    bnd = np.zeros((height, width), bool)
+    rx0, ry0, rx1, ry1 = (0, 0, width - 1, height - 1) if region is None else region
+    h, w = ry1 - ry0 + 1, rx1 - rx0 + 1
+    C = np.zeros((h, w, 3))
+    T = np.ones((h, w))
+    done = np.zeros((h, w), bool)
+    bnd = np.zeros((h, w), bool)
     for g in blend_order(p):
         x0, x1, y0, y1 = p.pix[g]
-        x0 = int(max(x0 - 2, 0)); x1 = int(min(x1 + 2, width - 1))
-        y0 = int(max(y0 - 2, 0)); y1 = int(min(y1 + 2, height - 1))
+        x0 = int(max(x0 - 2, rx0)); x1 = int(min(x1 + 2, rx1))
+        y0 = int(max(y0 - 2, ry0)); y1 = int(min(y1 + 2, ry1))
         if x0 > x1 or y0 > y1:
             continue
         ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
@@ -574,18 +591,24 @@ def render_image(p: Projected, width: int, height: int):
         A, B, Cc = p.conic[g]
         q = A * dx * dx + 2.0 * B * dx * dy + Cc * dy * dy
         al = np.minimum(ALPHA_MAX, p.opacity[g] * np.exp(-0.5 * q))
-        live = ~done[y0:y1 + 1, x0:x1 + 1]
-        bnd[y0:y1 + 1, x0:x1 + 1] |= live & (np.abs(al - ALPHA_MIN) <= ALPHA_BAND * ALPHA_MIN)
+        sl = (slice(y0 - ry0, y1 - ry0 + 1), slice(x0 - rx0, x1 - rx0 + 1))
+        live = ~done[sl]
+        bnd[sl] |= live & (np.abs(al - ALPHA_MIN) <= ALPHA_BAND * ALPHA_MIN)
         use = live & (al >= ALPHA_MIN)
-        t = T[y0:y1 + 1, x0:x1 + 1]
+        t = T[sl]
         tn = t * (1.0 - al)
-        bnd[y0:y1 + 1, x0:x1 + 1] |= use & (np.abs(tn - T_STOP) <= T_BAND * T_STOP)
+        bnd[sl] |= use & (np.abs(tn - T_STOP) <= T_BAND * T_STOP)
         stop = use & (tn < T_STOP)
         add = use & ~stop
-        C[y0:y1 + 1, x0:x1 + 1] += np.where(add[..., None], (al * t)[..., None] * p.rgb[g], 0.0)
-        T[y0:y1 + 1, x0:x1 + 1] = np.where(add, tn, t)
-        done[y0:y1 + 1, x0:x1 + 1] |= stop
+        C[sl] += np.where(add[..., None], (al * t)[..., None] * p.rgb[g], 0.0)
+        T[sl] = np.where(add, tn, t)
+        done[sl] |= stop
     return C, T, bnd
+
+
+def subset_projected(p: Projected, idx) -> Projected:
+    """The listed Gaussians of ``p`` (blend order among them is unchanged)."""
+    return Projected(**{k: getattr(p, k)[idx] for k in Projected.__dataclass_fields__})
 
 
 def psnr(a: np.ndarray, b: np.ndarray) -> float:

@@ -25,6 +25,7 @@ V3DG_OPT_ATTR_FP16 = 7
 V3DG_OPT_SELECT_TOPDOWN = 8
 V3DG_OPT_BLEND_BATCH = 9
 V3DG_OPT_GRAPHS = 10
+V3DG_OPT_BLEND_MODE = 11
 
 
 class V3dgError(RuntimeError):
@@ -60,7 +61,8 @@ class v3dg_stats(ctypes.Structure):
     _fields_ = [("cut_nodes", ctypes.c_uint64), ("cut_gaussians", ctypes.c_uint64),
                 ("render_nodes", ctypes.c_uint64), ("visible", ctypes.c_uint64), ("pairs", ctypes.c_uint64),
                 ("overflow", ctypes.c_uint32), ("timeout", ctypes.c_uint32),
-                ("blend_evals", ctypes.c_uint64), ("blend_contribs", ctypes.c_uint64)]
+                ("blend_evals", ctypes.c_uint64), ("blend_contribs", ctypes.c_uint64),
+                ("conic_fp64", ctypes.c_uint64)]
 
 
 class v3dg_request(ctypes.Structure):
@@ -101,9 +103,11 @@ SIGNATURES = {
     "v3dg_get_pairs": (_I32, [_P, _U64, ctypes.POINTER(_U64), _P, _P, _P, _P]),
     "v3dg_get_tile_ranges": (_I32, [_P, _P, _U64, ctypes.POINTER(_U64)]),
     "v3dg_stage_times": (_I32, [_P, _P, _I32, ctypes.POINTER(_U64)]),
-    "v3dg_autotune_blend": (_I32, [_P, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_F32)]),
+    "v3dg_autotune_blend": (_I32, [_P, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32),
+                                   ctypes.POINTER(_F32)]),
     "v3dg_sort_pairs": (_I32, [_P, _P, _P, _U64, _I32, _I32]),
     "v3dg_sort_pairs_noalloc": (_I32, [_P, _P, _U64, _I32, _I32, _P]),
+    "v3dg_check_wait": (_I32, [_P, _U32, _I32, ctypes.POINTER(_U32)]),
     "v3dg_server_start": (_I32, [_P, _I32, _U64]),
     "v3dg_server_stop": (_I32, [_P]),
     "v3dg_submit": (_I32, [_P, ctypes.POINTER(v3dg_request), ctypes.POINTER(_U64)]),
@@ -229,10 +233,10 @@ def v3dg_stage_times(ctx, ms_ptr: int | None, n: int) -> int:
     return launches.value
 
 
-def v3dg_autotune_blend(ctx) -> tuple[int, int, float]:
-    b, sp, ms = _U32(), _U32(), _F32()
-    _check(ctx, lib().v3dg_autotune_blend(ctx, ctypes.byref(b), ctypes.byref(sp), ctypes.byref(ms)))
-    return int(b.value), int(sp.value), float(ms.value)
+def v3dg_autotune_blend(ctx) -> tuple[int, int, int, float]:
+    m, b, sp, ms = _U32(), _U32(), _U32(), _F32()
+    _check(ctx, lib().v3dg_autotune_blend(ctx, ctypes.byref(m), ctypes.byref(b), ctypes.byref(sp), ctypes.byref(ms)))
+    return int(m.value), int(b.value), int(sp.value), float(ms.value)
 
 
 def v3dg_sort_pairs(ctx, keys_ptr: int, vals_ptr: int, n: int, begin_bit: int, end_bit: int) -> None:
@@ -245,6 +249,12 @@ def v3dg_sort_pairs_noalloc(keys_ptr: int, vals_ptr: int, n: int, begin_bit: int
                                        _P(stream_ptr) if stream_ptr else None)
     if st != V3DG_OK:
         raise V3dgError(st, f"v3dg_sort_pairs_noalloc(n={n}, bits [{begin_bit}, {end_bit}))")
+
+
+def v3dg_check_wait(ctx, spin_limit: int, predecessor_publishes: bool) -> int:
+    p = _U32()
+    _check(ctx, lib().v3dg_check_wait(ctx, spin_limit, 1 if predecessor_publishes else 0, ctypes.byref(p)))
+    return p.value
 
 
 def v3dg_server_start(ctx, slots: int, hbm_budget: int = 0) -> None:

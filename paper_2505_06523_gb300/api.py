@@ -205,12 +205,16 @@ class Context:
         return out
 
     def autotune_blend(self) -> dict:
-        """Time the last frame's blend with every batch size and split threshold and keep the
-        fastest (v3dg_autotune_blend)."""
-        b, sp, ms = N.v3dg_autotune_blend(self.ctx)
-        return {"batch": b, "split_pairs": sp, "ms": ms}
+        """Time the last frame's blend with every kernel variant, batch size and split threshold
+        and keep the fastest (v3dg_autotune_blend)."""
+        m, b, sp, ms = N.v3dg_autotune_blend(self.ctx)
+        return {"mode": m, "batch": b, "split_pairs": sp, "ms": ms}
 
-    # -- the sort on its own
+    def check_wait(self, spin_limit: int, predecessor_publishes: bool) -> int:
+        """The bounded-wait diagnostic (v3dg_check_wait); raises V3dgError(V3DG_ETIMEOUT) when the
+        look-back gives up."""
+        return N.v3dg_check_wait(self.ctx, spin_limit, predecessor_publishes)
+
     # -- serving
     def server_start(self, slots: int = 4, hbm_budget: int = 0):
         N.v3dg_server_start(self.ctx, int(slots), int(hbm_budget))

@@ -41,7 +41,7 @@ __device__ __forceinline__ void chain_publish(uint64_t* status, uint32_t stride,
 // look-back out of order (a tile passes every earlier one that has only its aggregate).
 template <int kW = 1>
 __device__ __forceinline__ uint32_t chain_lookback(uint64_t* status, uint32_t stride, uint32_t tile, uint32_t agg,
-                                                   uint32_t epoch, uint32_t* err) {
+                                                   uint32_t epoch, uint32_t* err, uint32_t spin_limit = kSpinLimit) {
   if (tile == 0) return 0;
   uint32_t excl = 0;
   int64_t j = int64_t(tile) - 1;
@@ -68,7 +68,7 @@ __device__ __forceinline__ uint32_t chain_lookback(uint64_t* status, uint32_t st
     if (done) break;
     j -= used;
     if (wait) {
-      if (++spins > kSpinLimit) {
+      if (++spins > spin_limit) {
         atomicOr(err, 1u);
         break;
       }
@@ -83,7 +83,8 @@ __device__ __forceinline__ uint32_t chain_lookback(uint64_t* status, uint32_t st
 // word of tile j - i, so each round covers 32 tiles; the nearest inclusive prefix or unwritten
 // word ends the round.  Returns the exclusive prefix in every lane; lane 0 publishes.
 __device__ __forceinline__ uint32_t chained_exclusive_warp(uint64_t* status, uint32_t tile, uint32_t agg,
-                                                           uint32_t epoch, uint32_t* err) {
+                                                           uint32_t epoch, uint32_t* err,
+                                                           uint32_t spin_limit = kSpinLimit) {
   const uint32_t lane = threadIdx.x & 31u;
   if (lane == 0) chain_publish(status, 1, tile, agg, epoch);
   if (tile == 0) return 0;
@@ -107,7 +108,7 @@ __device__ __forceinline__ uint32_t chained_exclusive_warp(uint64_t* status, uin
     if (first_prefix < first_wait) break;
     j -= take;
     if (take == 0) {
-      if (++spins > kSpinLimit) {
+      if (++spins > spin_limit) {
         if (lane == 0) atomicOr(err, 1u);
         break;
       }

@@ -81,6 +81,7 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
   }
   __syncthreads();
   const uint32_t base = s_base;
+  if (threadIdx.x == 0 && total) atomicAdd(reinterpret_cast<unsigned long long*>(frame + kPairs64), total);
   const bool fits = uint64_t(base) + total <= cap_pairs;   // else the frame overflows: count, write nothing
   if (!fits && threadIdx.x == 0) atomicOr(frame + kOverflow, 1u);
   // Each warp writes one contiguous range of the tile's pairs, 32 positions per step.  The owner
@@ -134,6 +135,12 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
 // After duplication: the pair count that later stages use (none when the frame overflowed, so
 // that no stage reads pair slots that were not written).
 __global__ void k_pairs_eff(uint32_t* frame, uint32_t cap_pairs) {
+  // a total beyond the capacity (counted in 64 bits, so also one beyond 2^32) overflows the frame
+  const unsigned long long total = *reinterpret_cast<const unsigned long long*>(frame + kPairs64);
+  if (total > cap_pairs) {
+    frame[kOverflow] = 1u;
+    frame[kPairs] = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(total);
+  }
   frame[kPairsEff] = frame[kOverflow] ? 0u : min(frame[kPairs], cap_pairs);
 }
 

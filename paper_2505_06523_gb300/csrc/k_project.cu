@@ -76,7 +76,8 @@ __device__ __forceinline__ uint32_t project_node(int lane, uint32_t ci, uint32_t
                                                  const CamConst& cam, const float4 bc, const float4 r0,
                                                  const float4 r1, int nsh, const float* __restrict__ at,
                                                  const TC* __restrict__ col, float4* __restrict__ rec,
-                                                 uint2* __restrict__ rect, uint32_t* __restrict__ keys) {
+                                                 uint2* __restrict__ rect, uint32_t* __restrict__ keys,
+                                                 uint32_t* __restrict__ frame) {
   const bool comp = r1.w != 0.f;
   constexpr size_t st = kSlots;   // values between planes
   uint32_t nvis = 0;
@@ -150,7 +151,8 @@ __device__ __forceinline__ uint32_t project_node(int lane, uint32_t ci, uint32_t
       ia = cc * id;
       ib = -cb * id;
       ic = ca * id;
-    } else {  // near-singular: form and invert Sigma_2D in FP64
+    } else {  // near-singular: form and invert Sigma_2D in FP64 (rare: counted)
+      atomicAdd(frame + kConicFp64, 1u);
       const double d00 = double(T00), d01 = double(T01), d02 = double(T02);
       const double d10 = double(T10), d11 = double(T11), d12 = double(T12);
       const double e01 = d00 * d11 - d01 * d10, e02 = d00 * d12 - d02 * d10, e12 = d01 * d12 - d02 * d11;
@@ -243,10 +245,10 @@ k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* _
     const unsigned char* col = blk + size_t(kGeoPlanes) * kSlots * 4;   // colour planes
     if (kFormats == 2 || (kFormats == 3 && A.half_color))
       nvis += project_node<__half>(lane, ci, cnt, I, cam, bc, r0, r1, A.sh_coeffs, at,
-                                   reinterpret_cast<const __half*>(col), rec, rect, keys);
+                                   reinterpret_cast<const __half*>(col), rec, rect, keys, frame);
     else
       nvis += project_node<float>(lane, ci, cnt, I, cam, bc, r0, r1, A.sh_coeffs, at,
-                                  reinterpret_cast<const float*>(col), rec, rect, keys);
+                                  reinterpret_cast<const float*>(col), rec, rect, keys, frame);
   }
   // one atomic per block for the visible count
 #pragma unroll

@@ -118,7 +118,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint16_t s_wh[kWarps][kBins];   // per-warp digit counts, then per-warp exclusive offsets
   __shared__ uint32_t s_start[kBins];        // block-local start of each digit
-  __shared__ int32_t s_goff[kBins];          // global destination offset minus local start
+  __shared__ uint32_t s_goff[kBins];         // global destination offset minus local start (mod 2^32)
   __shared__ uint32_t s_cnt[kBins];          // the tile's digit counts
   __shared__ uint32_t s_scan[kWarps + 1];
   __shared__ uint32_t s_tile;
@@ -215,19 +215,37 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   }
   if (tid <= dmask) {   // (the digit's count and start reloaded: no registers held over the reorder)
     const uint32_t excl = chain_lookback<kLookback>(status + tid, kBins, tile, s_cnt[tid], epoch, err);
-    s_goff[tid] = int32_t(gexcl[tid] + excl) - int32_t(s_start[tid]);
+    s_goff[tid] = gexcl[tid] + excl - s_start[tid];   // wraps; dst = s_goff + p is exact below 2^32
   }
   __syncthreads();
   const uint32_t valid = min(uint32_t(kSortTile), n - tile * kSortTile);
 #pragma unroll 4
   for (uint32_t p = tid; p < valid; p += kSortThreads) {
     const uint32_t k = s_keys[p];
-    const uint32_t dst = uint32_t(s_goff[(k >> shift) & dmask] + int32_t(p));
+    const uint32_t dst = s_goff[(k >> shift) & dmask] + p;
     kout[dst] = k;
     vout[dst] = s_vals[p];
   }
   __syncthreads();   // the tile's shared data is consumed before the next tile reuses it
   }  // next tile
+}
+
+// Diagnostic of the bounded waits: warp 0 runs the radix-sort passes' look-back (one thread,
+// kLookback words per round), warp 1 the warp-wide look-back of the compaction and expansion
+// kernels, each as tile 1 of its own two-word chain whose tile 0 publishes the prefix 1000 + warp
+// (publish != 0) or never publishes (its word keeps an epoch that is not `epoch`).
+__global__ void k_check_wait(uint64_t* __restrict__ status, uint32_t epoch, uint32_t spin_limit, int publish,
+                             uint32_t* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t* chain = status + 2 * warp;
+  if (lane == 0 && publish) chain_publish(chain, 1, 0, 1000u + uint32_t(warp), epoch);
+  __syncwarp();
+  if (warp == 0) {
+    if (lane == 0) out[0] = chain_lookback<kLookback>(chain, 1, 1, 1u, epoch, out + 2, spin_limit);
+  } else {
+    const uint32_t e = chained_exclusive_warp(chain, 1, 1u, epoch, out + 2, spin_limit);
+    if (lane == 0) out[1] = e;
+  }
 }
 
 }  // namespace
@@ -286,6 +304,12 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
   }
   *result_in_1 = (passes & 1) != 0;
   return cudaSuccess;
+}
+
+cudaError_t launch_check_wait(uint64_t* status, uint32_t epoch, uint32_t spin_limit, int publish, uint32_t* out,
+                              cudaStream_t st) {
+  k_check_wait<<<1, 64, 0, st>>>(status, epoch, spin_limit, publish, out);
+  return cudaGetLastError();
 }
 
 }  // namespace v3dg

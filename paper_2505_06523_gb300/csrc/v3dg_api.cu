@@ -50,8 +50,8 @@ struct AssetHost {
 
 constexpr uint32_t kInitNodes = 1u << 14;
 constexpr uint32_t kInitPairs = 1u << 22;
-constexpr uint32_t kMaxNodes = 1u << 24;
-constexpr uint32_t kMaxPairs = (1u << 31) - 1u;
+constexpr uint32_t kMaxNodes = 1u << 25;               // render-list clusters: at most 2^31 slots
+constexpr uint32_t kMaxPairs = 0xFFFFFFFFu - 4096u;    // pair indices are 32-bit (a sort tile of headroom)
 enum { kStageSelect = 0, kStageProject, kStageDepthSort, kStageBin, kStageTileSort, kStageRanges, kStageBlend, kStages };
 
 }  // namespace
@@ -117,6 +117,7 @@ struct v3dg_ctx {
   bool attr_fp16 = false;   // store opacity and SH of the next loaded assets as float16
   int topdown = 2;          // 0 flat, 1 level by level from the roots (same cut), 2 top-down for large scenes
   int blend_batch = 512;    // records staged per blend batch: 128, 256 or 512
+  int blend_mode = 0;       // 0: two-phase blend; 1: bulk-copy staging, warps composite row pairs
   bool graphs = false;      // capture each frame's launches once and replay them as a CUDA graph
   Pipe main;
   Server* server = nullptr;
@@ -424,7 +425,9 @@ v3dg_status enqueue_select(Pipe* c) {
 // list overflow still invalidates the frame) and count the slots the depth sort covers.
 __global__ void k_render_reset(uint32_t* frame, uint32_t cap_nodes) {
   const int i = threadIdx.x;
-  if (i == kVisible || i == kPairs || i == kPairsEff || (i > kTileCounters && i < kFrameWords)) frame[i] = 0;
+  if (i == kVisible || i == kPairs || i == kPairsEff || i == kConicFp64 || i == kPairs64 || i == kPairs64 + 1 ||
+      (i > kTileCounters && i < kFrameWords))
+    frame[i] = 0;
   if (i == kSlotCount) frame[kSlotCount] = min(frame[kRenderNodes], cap_nodes) * uint32_t(kSlots);
 }
 
@@ -490,7 +493,7 @@ v3dg_status enqueue_render(Pipe* c, float* rgb, float* t_out) {
   // d_misc[12], [13]: sticky overflow / timeout flags of all frames since the last v3dg_frame_stats
   CU(launch_blend(P<uint2>(c->d_ranges), P<uint32_t>(c->d_order), frame + kTileCounters + 10, tk, tv, P<float4>(c->d_rec),
                   c->cap_slots, k, rgb, t_out, work, frame, P<uint32_t>(c->d_misc) + 12, c->ctx->split_pairs,
-                  c->ctx->blend_batch, int(c->n_views), sm, c->stream));
+                  c->ctx->blend_batch, c->ctx->blend_mode, int(c->n_views), sm, c->stream));
   c->ctx->launches += 2;
   if (work)
     CU(cudaMemcpyAsync(c->h_tmp + kFrameWords, work, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
@@ -507,15 +510,16 @@ v3dg_status grow_and_reselect(Pipe* c) {
   const uint32_t* f = c->h_frame;
   bool grew = false;
   if (f[kRenderNodes] > c->cap_nodes) {
-    const uint64_t want = uint64_t(f[kRenderNodes]) * 5 / 4 + 1024;
-    if (want > kMaxNodes) return fail(c, V3DG_EOVERFLOW, "render list of %u nodes exceeds the limit", f[kRenderNodes]);
-    c->cap_nodes = uint32_t(want);
+    if (f[kRenderNodes] > kMaxNodes)
+      return fail(c, V3DG_EOVERFLOW, "render list of %u nodes exceeds the limit", f[kRenderNodes]);
+    c->cap_nodes = uint32_t(std::min<uint64_t>(uint64_t(f[kRenderNodes]) * 5 / 4 + 1024, kMaxNodes));
     grew = true;
   }
   if (f[kPairs] >= c->cap_pairs || !grew) {
+    if (f[kPairs] > kMaxPairs || c->cap_pairs >= kMaxPairs)
+      return fail(c, V3DG_EOVERFLOW, "%u pairs exceed the limit of %u", f[kPairs], kMaxPairs);
     const uint64_t want = std::max<uint64_t>(uint64_t(f[kPairs]) * 5 / 4, uint64_t(c->cap_pairs) * 2);
-    if (want > kMaxPairs) return fail(c, V3DG_EOVERFLOW, "%u pairs exceed the limit", f[kPairs]);
-    c->cap_pairs = uint32_t(want);
+    c->cap_pairs = uint32_t(std::min<uint64_t>(want, kMaxPairs));
   }
   CU(cudaMemsetAsync(P<uint32_t>(c->d_misc) + 12, 0, 2 * sizeof(uint32_t), c->stream));
   ST(enqueue_select(c));
@@ -547,7 +551,8 @@ std::vector<uint64_t> graph_key(Pipe* c, float* rgb, float* t_out) {
   const v3dg_ctx* ctx = c->ctx;
   std::vector<uint64_t> k = {c->n_inst_frame, c->n_views, uint64_t(c->node_blocks), c->cap_nodes, c->cap_pairs,
                              c->cap_slots, c->status_words, uint64_t(uintptr_t(rgb)), uint64_t(uintptr_t(t_out)),
-                             uint64_t(use_topdown(c)), uint64_t(ctx->blend_batch), ctx->split_pairs,
+                             uint64_t(use_topdown(c)), uint64_t(ctx->blend_batch), uint64_t(ctx->blend_mode),
+                             ctx->split_pairs,
                              uint64_t(ctx->count_work), uint64_t(c->color_formats), ctx->assets.size(),
                              uint64_t(uintptr_t(ctx->d_assets.p))};
   const DevBuf* bufs[] = {&c->d_inst, &c->d_frame, &c->d_misc, &c->d_list, &c->d_ref, &c->d_keys0, &c->d_keys1,
@@ -961,6 +966,10 @@ v3dg_status v3dg_set_option(v3dg_ctx* ctx, int option, int64_t value) {
       if (value != 128 && value != 256 && value != 512) return fail(c, V3DG_EINVAL, "blend batch must be 128, 256 or 512");
       ctx->blend_batch = int(value);
       break;
+    case V3DG_OPT_BLEND_MODE:
+      if (value != 0 && value != 1) return fail(c, V3DG_EINVAL, "blend mode must be 0 or 1");
+      ctx->blend_mode = int(value);
+      break;
     case V3DG_OPT_SPLIT_PAIRS:
       if (value < 1 || value > 0xFFFFFFFFll) return fail(c, V3DG_EINVAL, "split threshold out of range");
       ctx->split_pairs = uint32_t(value);
@@ -1229,6 +1238,7 @@ v3dg_status v3dg_frame_stats(v3dg_ctx* ctx, v3dg_stats* out) {
   out->render_nodes = f[kRenderNodes];
   out->visible = f[kVisible];
   out->pairs = f[kPairs];
+  out->conic_fp64 = f[kConicFp64];
   uint32_t sticky[2] = {0, 0};
   CU(cudaMemcpy(sticky, P<uint32_t>(c->d_misc) + 12, sizeof sticky, cudaMemcpyDeviceToHost));
   CU(cudaMemset(P<uint32_t>(c->d_misc) + 12, 0, sizeof sticky));
@@ -1386,7 +1396,8 @@ v3dg_status v3dg_stage_times(v3dg_ctx* ctx, float* ms, int n, uint64_t* launches
   return V3DG_OK;
 }
 
-v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* batch_out, uint32_t* split_out, float* ms_out) {
+v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* mode_out, uint32_t* batch_out, uint32_t* split_out,
+                                float* ms_out) {
   Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
   if (!c->rendered) return fail(c, V3DG_ENOTFOUND, "no frame rendered");
@@ -1407,11 +1418,13 @@ v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* batch_out, uint32_t* sp
   const int batches[] = {128, 256, 512};
   const uint32_t splits[] = {4096u, 16384u, 65536u, 0xFFFFFFFFu};
   float best = INFINITY;
-  int best_b = ctx->blend_batch;
+  int best_b = ctx->blend_batch, best_m = ctx->blend_mode;
   uint32_t best_s = ctx->split_pairs;
   cudaError_t e = cudaSuccess;
+  for (int mode = 0; mode < 2; ++mode)
   for (int b : batches) {
     for (uint32_t sp : splits) {
+      if (mode == 1 && sp != 0xFFFFFFFFu) continue;   // that variant always blends whole tiles
       float t_min = INFINITY;
       for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // the first run warms up
         e = cudaMemsetAsync(frame + kTileCounters + 10, 0, sizeof(uint32_t), c->stream);
@@ -1419,7 +1432,7 @@ v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* batch_out, uint32_t* sp
         if (e == cudaSuccess)
           e = launch_blend(P<uint2>(c->d_ranges), P<uint32_t>(c->d_order), frame + kTileCounters + 10, tk, tv,
                            P<float4>(c->d_rec), c->cap_slots, k, P<float>(c->d_img), nullptr, nullptr, frame,
-                           P<uint32_t>(c->d_misc) + 12, sp, b, int(c->n_views), ctx->sm_count, c->stream);
+                           P<uint32_t>(c->d_misc) + 12, sp, b, mode, int(c->n_views), ctx->sm_count, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -1431,6 +1444,7 @@ v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* batch_out, uint32_t* sp
         best = t_min;
         best_b = b;
         best_s = sp;
+        best_m = mode;
       }
     }
   }
@@ -1439,6 +1453,8 @@ v3dg_status v3dg_autotune_blend(v3dg_ctx* ctx, uint32_t* batch_out, uint32_t* sp
   if (e != cudaSuccess) return fail(c, V3DG_ECUDA, "CUDA error %s", cudaGetErrorString(e));
   ctx->blend_batch = best_b;
   ctx->split_pairs = best_s;
+  ctx->blend_mode = best_m;
+  if (mode_out) *mode_out = uint32_t(best_m);
   if (batch_out) *batch_out = uint32_t(best_b);
   if (split_out) *split_out = best_s;
   if (ms_out) *ms_out = best;
@@ -1475,6 +1491,28 @@ v3dg_status v3dg_sort_pairs(v3dg_ctx* ctx, uint32_t* keys, uint32_t* vals, uint6
   CU(cudaMemcpyAsync(c->h_tmp, misc + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   if (c->h_tmp[0]) return fail(c, V3DG_ETIMEOUT, "a bounded device-side wait gave up; output invalid");
+  c->err.clear();
+  return V3DG_OK;
+}
+
+v3dg_status v3dg_check_wait(v3dg_ctx* ctx, uint32_t spin_limit, int predecessor_publishes, uint32_t* prefix) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
+  if (!c) return V3DG_EINVAL;
+  if (spin_limit < 1 || spin_limit > kSpinLimit)
+    return fail(c, V3DG_EINVAL, "spin_limit must be in [1, %u]", kSpinLimit);
+  CU(cudaSetDevice(ctx->device));
+  ST(ensure_status(c, std::max<uint64_t>(c->status_words, 4)));
+  uint32_t* out = P<uint32_t>(c->d_misc) + 16;   // d_misc[16..18]: the two prefixes and the gave-up flag
+  CU(cudaMemsetAsync(c->d_status.p, 0, 4 * sizeof(uint64_t), c->stream));   // epoch 0 is never a current epoch
+  CU(cudaMemsetAsync(out, 0, 3 * sizeof(uint32_t), c->stream));
+  CU(launch_check_wait(P<uint64_t>(c->d_status), next_epoch(c), spin_limit, predecessor_publishes, out, c->stream));
+  ++ctx->launches;
+  CU(cudaMemcpyAsync(c->h_tmp, out, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (prefix) *prefix = c->h_tmp[0];
+  if (c->h_tmp[2]) return fail(c, V3DG_ETIMEOUT, "the look-back gave up after %u polls", spin_limit);
+  if (c->h_tmp[0] != 1000u || c->h_tmp[1] != 1001u)
+    return fail(c, V3DG_ECUDA, "look-back prefixes %u, %u (expected 1000, 1001)", c->h_tmp[0], c->h_tmp[1]);
   c->err.clear();
   return V3DG_OK;
 }

@@ -77,6 +77,8 @@ enum Counter : int {
   kSlotCount = 7,          // render nodes (clamped) * 64: the slots the depth sort covers
   kPairsEff = 8,           // pairs the tile sort / blend use: kPairs, or 0 when the frame overflowed
   kTdReached = 9,          // top-down selection: (instance, node) entries it tested
+  kConicFp64 = 10,         // Gaussians whose 2D covariance had det < 1e-12 and was inverted in FP64
+  kPairs64 = 12,           // [12, 14): the pair total as a 64-bit sum (detects totals beyond 2^32)
   kNumCounters = 16,
   kTileCounters = 16,      // [16, 48): atomic tile counters of the chained-scan kernels
   kFrameWords = 48,
@@ -85,6 +87,13 @@ enum Counter : int {
 // Status words of the chained (decoupled look-back) scans: epoch << 34 | flag << 32 | value.
 constexpr uint64_t kFlagAgg = 1, kFlagPrefix = 2;
 constexpr uint32_t kSpinLimit = 1u << 20;
+
+// Diagnostic of the bounded waits: one look-back as tile 1 of a two-tile chain whose tile 0
+// publishes (publish != 0) or never does, with at most spin_limit polls, by one thread and by a
+// whole warp.  out[0], out[1]: the prefixes the two look-backs found; out[2]: nonzero if a wait
+// gave up.  status: 2 * 2 words.
+cudaError_t launch_check_wait(uint64_t* status, uint32_t epoch, uint32_t spin_limit, int publish, uint32_t* out,
+                              cudaStream_t st);
 
 // ---------------------------------------------------------------- launch functions (return cudaError)
 // Selection (Sec. 3.3-3.4).  mode 0: render list (cut minus the visibility cull) + counters;
@@ -178,9 +187,12 @@ cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const u
 // tile_counter: a zeroed word.  batch: records staged per batch, 128, 256 or 512.  n_views
 // images of cam's size, one after the other in rgb (and t_out); tile ids are (view, tile).
 // tk, pair_vals: the sorted pair keys (tile id and in-tile box, see kPairTileMask) and values.
+// mode 0: two-phase blend (record-parallel alpha test into per-pixel masks, then pixel-parallel
+// compositing); mode 1: batches staged by bulk copies and composited by warps over row pairs.  The
+// image is the same bit for bit.
 cudaError_t launch_blend(const uint2* ranges, uint32_t* items, uint32_t* tile_counter, const uint32_t* tk,
                          const uint32_t* pair_vals, const float4* rec, uint32_t cap_slots, const CamConst& cam, float* rgb, float* t_out,
-                         unsigned long long* work, const uint32_t* frame, uint32_t* sticky, uint32_t split_pairs,
-                         int batch, int n_views, int sm_count, cudaStream_t st);
+                         unsigned long long* work, uint32_t* frame, uint32_t* sticky, uint32_t split_pairs,
+                         int batch, int mode, int n_views, int sm_count, cudaStream_t st);
 
 }  // namespace v3dg

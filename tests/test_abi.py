@@ -33,11 +33,34 @@ def test_binding_covers_the_header(native):
     assert set(_declared()) == set(native.SIGNATURES)
 
 
-def test_struct_sizes_match_the_header(native):
+def test_struct_sizes_match_the_header(native, tmp_path):
+    """The ctypes structures have the sizes and field offsets that a C compiler gives the header's
+    structures (compiled here with the host C compiler)."""
     import ctypes
-    # v3dg_camera: 12 doubles + 4 floats + 2 int32 + float (+ padding to 8)
-    assert ctypes.sizeof(native.v3dg_camera) == 96 + 16 + 8 + 4 + 4
-    assert ctypes.sizeof(native.v3dg_stats) == 5 * 8 + 2 * 4 + 2 * 8
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"v3dg_camera": native.v3dg_camera, "v3dg_stats": native.v3dg_stats,
+               "v3dg_hierarchy_desc": native.v3dg_hierarchy_desc, "v3dg_request": native.v3dg_request,
+               "v3dg_result": native.v3dg_result, "v3dg_allocator": native.v3dg_allocator}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "v3dg.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        name, field, value = line.split()
+        cls = structs[name]
+        got = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert got == int(value), (name, field, got, value)
 
 
 def test_no_gpu_means_an_error_not_a_fallback(native):

@@ -6,8 +6,8 @@ import pytest
 
 import oracle
 from synth import scenes
-from v3dg_cases import (IMG_ABS, PSNR_MIN, assert_cut_parity, assert_pairs_parity, assert_projection_parity,
-                        image_errors)
+from v3dg_cases import (IMG_ABS, PSNR_MIN, assert_cut_parity, assert_image_matches_oracle, assert_pairs_parity,
+                        assert_projection_parity, image_errors)
 
 pytestmark = pytest.mark.gpu
 
@@ -246,12 +246,13 @@ def test_paper_shaped_bundle(Context, view, tau):
 
 
 def test_blend_batch_sizes_and_autotuner(Context, tiny_asset, small_asset):
-    """Every blend batch size gives the same image bit for bit; the autotuner needs a rendered
-    frame, picks one of its candidates, keeps it, and the frames after it are unchanged."""
-    from paper_2505_06523_gb300._native import V3DG_OPT_BLEND_BATCH, V3dgError
+    """Every blend variant and batch size gives the same image bit for bit; the autotuner needs a
+    rendered frame, picks one of its candidates, keeps it, and the frames after it are unchanged."""
+    from paper_2505_06523_gb300._native import V3DG_OPT_BLEND_BATCH, V3DG_OPT_BLEND_MODE, V3dgError
     inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
     cam = scenes.crowd_camera(40, 640, 360)
-    outs = [_frame(Context, [tiny_asset, small_asset], inst, cam, 1.0, {V3DG_OPT_BLEND_BATCH: b}) for b in (128, 256, 512)]
+    outs = [_frame(Context, [tiny_asset, small_asset], inst, cam, 1.0, {V3DG_OPT_BLEND_BATCH: b, V3DG_OPT_BLEND_MODE: m})
+            for m in (0, 1) for b in (128, 256, 512)]
     assert float(np.abs(outs[0]["rgb"]).sum()) > 0
     for o in outs[1:]:
         assert (o["rgb"] == outs[0]["rgb"]).all() and (o["T"] == outs[0]["T"]).all()
@@ -265,9 +266,12 @@ def test_blend_batch_sizes_and_autotuner(Context, tiny_asset, small_asset):
         ctx.render()
         r = ctx.autotune_blend()
         assert r["batch"] in (128, 256, 512) and r["split_pairs"] in (4096, 16384, 65536, 0xFFFFFFFF) and r["ms"] > 0
+        assert r["mode"] in (0, 1)
         ctx.select(cam, 1.0)
         rgb, T = ctx.render(want_T=True)
         assert (rgb.cpu().numpy() == outs[0]["rgb"]).all() and (T.cpu().numpy() == outs[0]["T"]).all()
+    # the frame rendered with the tuned settings, against the oracle itself
+    assert_image_matches_oracle(rgb.cpu().numpy(), T.cpu().numpy(), [tiny_asset, small_asset], inst, cam, 1.0)
 
 
 def test_views_batch_equals_single_views(Context, tiny_asset, small_asset):
@@ -297,6 +301,8 @@ def test_views_batch_equals_single_views(Context, tiny_asset, small_asset):
         assert np.array_equal(mine, one["cut"])
         rv = ranges[v * 510:(v + 1) * 510].astype(np.int64)
         assert ((rv[:, 1] - rv[:, 0]) == (one["ranges"][:, 1].astype(np.int64) - one["ranges"][:, 0])).all()
+    for v in (0, 2):   # views of the batch against the oracle itself
+        assert_image_matches_oracle(rgb[v], T[v], assets, inst, cams[v], 1.0)
     with pytest.raises(Exception):
         with Context(0) as ctx:
             ctx.load_hierarchy(tiny_asset)
@@ -330,6 +336,9 @@ def test_graph_frames_match_launch_by_launch(Context, tiny_asset, small_asset):
     assert float(np.abs(out[0][0][0]).sum()) > 0
     for (r0, t0, p0, n0), (r1, t1, p1, n1) in zip(out[0], out[1]):
         assert (r0 == r1).all() and (t0 == t1).all() and p0 == p1 and n0 == n1
+    for k in (1, 4, 6):   # graph replays (one after a size change) against the oracle itself
+        cam = (cams + cams[:2])[k]
+        assert_image_matches_oracle(out[1][k][0], out[1][k][1], [tiny_asset, small_asset], inst, cam, 1.0)
 
 
 def test_views_topdown_graph_batch512_together(Context, tiny_asset, small_asset):
@@ -353,3 +362,5 @@ def test_views_topdown_graph_batch512_together(Context, tiny_asset, small_asset)
             rgb, T = rgb.cpu().numpy(), T.cpu().numpy()
             for v, one in enumerate(singles):
                 assert (rgb[v] == one["rgb"]).all() and (T[v] == one["T"]).all(), v
+    for v, cam in enumerate(cams):   # and each view against the oracle itself
+        assert_image_matches_oracle(rgb[v], T[v], assets, inst, cam, 1.0)

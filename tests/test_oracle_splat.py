@@ -120,6 +120,56 @@ def test_instance_equals_world_gaussian():
     np.testing.assert_allclose(pa.cov, pw.cov, rtol=1e-4, atol=1e-9)
 
 
+def _rotate_sh(sh, rot, rng):
+    """SH coefficients (k, 16, 3) of the colour field d -> f(R^T d), i.e. the asset's colour field
+    carried into the world frame by the rotation R.
+
+    Band 1 by its closed form: with Y_1 = k1 (-y, z, -x), the field is k1 w . d with
+    w = (-c_{1,1}, -c_{1,-1}, c_{1,0}), and f(R^T d) = k1 (R w) . d.  Bands 2 and 3 by least squares
+    over random directions (each band is closed under rotation, so the fit is exact)."""
+    out = np.array(sh, np.float64, copy=True)
+    w = np.stack([-sh[:, 3, :], -sh[:, 1, :], sh[:, 2, :]], axis=1)       # (k, 3, channel)
+    ww = np.einsum("ij,kjc->kic", rot, w)
+    out[:, 3, :], out[:, 1, :], out[:, 2, :] = -ww[:, 0, :], -ww[:, 1, :], ww[:, 2, :]
+    d = rng.normal(size=(400, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    y_w, y_a = oracle.sh_basis(d), oracle.sh_basis(d @ rot)               # rows: Y(d), Y(R^T d)
+    for band in (slice(4, 9), slice(9, 16)):
+        m, *_ = np.linalg.lstsq(y_w[:, band], y_a[:, band], rcond=None)   # Y_a = Y_w m
+        out[:, band, :] = np.einsum("ij,kjc->kic", m, sh[:, band, :])
+    return out
+
+
+def test_instance_sh_view_direction():
+    """The colour of an instanced Gaussian is evaluated along the view direction in the asset
+    frame, R^T (mu_world - C) / |...|: an instance (s, R, t) with degree-1..3 SH gives the colour
+    of the directly placed world Gaussian whose SH field is rotated by R.  A direction taken in
+    the world frame, rotated by R instead of R^T, or without removing s and t, changes the colour
+    by far more than the tolerance."""
+    rng = np.random.default_rng(13)
+    cam = scenes.look_at((0.7, -3.2, 1.1), (0.1, 0.2, 0.0), 128, 96, 50.0)
+    n = 24
+    mu = rng.normal(0, 0.5, (n, 3))
+    ls = rng.normal(-3, 0.4, (n, 3))
+    q = rng.normal(size=(n, 4))
+    sh = rng.normal(0, 0.4, (n, 16, 3))
+    rot = scenes.random_rotations(rng, 1)
+    t = np.array([[0.3, -0.4, 0.2]])
+    s = 1.7
+    inst = scenes.Instances(np.zeros(1, np.uint32), rot, t, np.array([s]))
+    pa = project_all(one_node_asset(mu, ls, q, sh=sh), cam, inst)
+    sh32 = np.asarray(sh, np.float32).astype(np.float64)
+    mu_w = (s * (rot[0] @ mu.astype(np.float32).astype(np.float64).T)).T + t[0]
+    rq = _rot_to_quat(rot[0])
+    qw = np.array([_qmul(rq, qq / np.linalg.norm(qq)) for qq in q.astype(np.float32).astype(np.float64)])
+    pw = project_all(one_node_asset(mu_w, ls + math.log(s), qw, sh=_rotate_sh(sh32, rot[0], rng)), cam)
+    assert pa.visible.sum() > n // 2
+    np.testing.assert_allclose(pa.rgb, pw.rgb, rtol=0, atol=2e-5)
+    # the test is sensitive: the same Gaussians with the unrotated SH differ clearly
+    pu = project_all(one_node_asset(mu_w, ls + math.log(s), qw, sh=sh32), cam)
+    assert np.abs(pa.rgb - pu.rgb).max() > 0.05
+
+
 def _qmul(a, b):
     w1, x1, y1, z1 = a
     w2, x2, y2, z2 = b
@@ -265,6 +315,23 @@ def test_pixelwise_equals_gaussianwise():
     assert (B.ravel() == b).all()
 
 
+def test_regions_stitch_into_the_image():
+    """Tiling is only an acceleration: regions rendered on their own (each from just the Gaussians
+    whose box reaches it) stitch into the whole image exactly."""
+    a, cam, p = _random_scene(10, n=60, w=50, h=37)
+    C, T, B = oracle.render_image(p, cam.width, cam.height)
+    C2, T2, B2 = np.zeros_like(C), np.zeros_like(T), np.zeros_like(B)
+    for y0 in range(0, 37, 16):
+        for x0 in range(0, 50, 16):
+            x1, y1 = min(x0 + 15, 49), min(y0 + 15, 36)
+            near = (p.pix[:, 0] - 2 <= x1) & (p.pix[:, 1] + 2 >= x0) & (p.pix[:, 2] - 2 <= y1) & (p.pix[:, 3] + 2 >= y0)
+            c, t, b = oracle.render_image(oracle.subset_projected(p, np.nonzero(near)[0]), cam.width, cam.height,
+                                          region=(x0, y0, x1, y1))
+            C2[y0:y1 + 1, x0:x1 + 1], T2[y0:y1 + 1, x0:x1 + 1], B2[y0:y1 + 1, x0:x1 + 1] = c, t, b
+    assert np.array_equal(C, C2) and np.array_equal(T, T2) and np.array_equal(B, B2)
+    assert (T < 1).sum() > 200
+
+
 def test_tile_rect_covers_every_contribution():
     """Every pixel where a Gaussian reaches alpha >= 1/255 lies in a tile of its rectangle."""
     a, cam, p = _random_scene(7, n=60, w=64, h=48)
@@ -358,3 +425,16 @@ def test_nodes_reaching_pixels_keeps_every_contributor(small_asset):
         assert kept_g.issuperset((p.inst[hit].astype(np.int64) << 32 | p.local[hit].astype(np.int64)).tolist())
     c2, t2, b2 = oracle.render_pixels(pg, pix)
     assert np.array_equal(c0, c2) and np.array_equal(t0, t2) and np.array_equal(b0, b2)
+    # windows tested as wholes keep a superset, so the same contributors and the same pixels
+    drawn = [(px, py) for (px, py), tt in zip(pix, t0) if tt < 0.99]
+    wins = [(max(px - 6, 0), max(py - 6, 0), min(px + 6, 319), min(py + 6, 179)) for px, py in drawn[::max(1, len(drawn) // 3)][:3]]
+    wpix = [(x, y) for x0, y0, x1, y1 in wins for y in range(y0, y1 + 1) for x in range(x0, x1 + 1)]
+    sub_w, only_w = oracle.gaussians_reaching_pixels([small_asset], inst, cam, cut, wpix, windows=wins)
+    sub_p, only_p = oracle.gaussians_reaching_pixels([small_asset], inst, cam, cut, wpix)
+    for i, loc in only_p.items():
+        assert set(loc.tolist()) <= set(only_w.get(i, np.zeros(0)).tolist())
+    pw = oracle.project([small_asset], inst, cam, sub_w, only=only_w)
+    cw, tw, bw = oracle.render_pixels(pw, wpix)
+    cf, tf, bf = oracle.render_pixels(p, wpix)
+    assert np.array_equal(cw, cf) and np.array_equal(tw, tf) and np.array_equal(bw, bf)
+    assert (tf < 0.999).sum() > 50

@@ -5,11 +5,14 @@ import numpy as np
 
 import oracle
 
-# tolerances of the per-Gaussian records (the image bar is a max abs error of 1e-4 per channel)
-U_ABS_PX = 2e-3          # screen mean, px
-CONIC_REL = 2e-3         # relative to the largest conic entry
-RGB_ABS = 2e-5
-OPACITY_REL = 2e-6
+# Tolerances of the per-Gaussian records, about four times the largest errors measured against
+# the FP64 oracle on a GB300 (tiny asset from three cameras, 200-instance crowd at 640x360: screen
+# mean 7.6e-5 px, conic 2.0e-6 relative, colour 5.1e-7, opacity 2.1e-7).  The image bar is a max
+# abs error of 1e-4 per channel outside the decision bands (measured 3e-6) and PSNR >= 50 dB.
+U_ABS_PX = 3e-4          # screen mean, px
+CONIC_REL = 1e-5         # relative to the largest conic entry
+RGB_ABS = 2e-6
+OPACITY_REL = 1e-6
 IMG_ABS = 1e-4
 PSNR_MIN = 50.0
 
@@ -84,3 +87,17 @@ def assert_pairs_parity(g: dict, p: oracle.Projected, cam):
 def image_errors(img: np.ndarray, C: np.ndarray, B: np.ndarray):
     e = np.abs(img.astype(np.float64) - C).max(axis=-1)
     return float(e[~B].max()) if (~B).any() else 0.0, float(oracle.psnr(img, C)), int(B.sum())
+
+
+def assert_image_matches_oracle(rgb, T, assets, inst, cam, tau, cut=None):
+    """A rendered image (and its final transmittance) against the per-pixel definition, outside
+    the decision bands; PSNR over every pixel.  Returns (max abs error, PSNR, band pixels)."""
+    if cut is None:
+        cut = oracle.select(assets, inst, cam, tau)
+    p = oracle.project(assets, inst, cam, cut)
+    C, To, B = oracle.render_image(p, cam.width, cam.height)
+    err, ps, nb = image_errors(rgb, C, B)
+    assert err <= IMG_ABS and ps >= PSNR_MIN, (err, ps, nb)
+    if T is not None:
+        assert np.abs(np.asarray(T, np.float64) - To)[~B].max() <= IMG_ABS
+    return err, ps, nb
