@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=150)
     ap.add_argument("--views", type=int, default=16, help="views per launch of the batched leg (0: none)")
     ap.add_argument("--no-extra-legs", action="store_true", help="skip the orbit table and the no-LOD comparison")
+    ap.add_argument("--mix-seconds", type=float, default=2.5,
+                    help="seconds of Poisson arrivals per rate of the serving mix (config 5; 0: no mix leg)")
     return ap.parse_args()
 
 
@@ -466,9 +468,20 @@ def main():
                            {"mode": tuned["mode"], "batch": tuned["batch"], "split_pairs": tuned["split_pairs"]})
         served["autotune"] = tuned
         served["psnr_fp16_vs_fp32_db"] = fp16_psnr(ctx, inst, inst16, cams, timed_ids, args.tau)
+        if args.mix_seconds > 0:
+            sc32 = mix_scenes(inst, len(assets))
+            sc16 = {k: scenes.subset(v, np.arange(v.n)) for k, v in sc32.items()}
+            for v in sc16.values():
+                v.asset = v.asset + np.uint32(len(assets))
+            served["mix"] = serve_mix_leg(ctx, sc32, sc16, args.slots,
+                                          {"mode": tuned["mode"], "batch": tuned["batch"],
+                                           "split_pairs": tuned["split_pairs"]}, args.mix_seconds)
         if args.views > 0:
             served["batched"], view_samples = batched_leg(ctx, inst, inst16, cams, timed_ids, (1.0, 2.0), args.views,
                                                           tuned)
+            # the views' buffers (~100 GB at 16 crowd views) go back to the device before the next legs
+            ctx.release_buffers()
+            torch.cuda.empty_cache()
 
     extra = {}
     if not args.no_extra_legs:
@@ -615,6 +628,100 @@ def serve_leg(ctx, inst, inst16, cams, frame_ids, tau, slots, n_req, tuned):
     out["served_vs_plain"] = {
         "frames_per_s": cap["served"] / cap["plain"],
         "p99_at_90pct_load": out["served"]["poisson"][1]["p99_ms"] / out["plain"]["poisson"][1]["p99_ms"]}
+    return out
+
+
+MIX_RES = [(1280, 720), (1920, 1080), (3840, 2160)]
+MIX_TAUS = [0.5, 1.0, 2.0, 4.0]
+MIX_RATES = [30.0, 100.0, 250.0, 500.0]
+
+
+def mix_scenes(inst1000, n_assets):
+    """Config 5's scenes: 100 instances (the first of the crowd layout), the 1000-instance crowd,
+    and 5000 (the crowd extended by 4000 more instances from the same generator, seed 1001)."""
+    from synth import scenes
+    ext = scenes.crowd_instances(4000, n_assets=n_assets, seed=1001)
+    five = scenes.Instances(np.concatenate([inst1000.asset, ext.asset]), np.concatenate([inst1000.rot, ext.rot]),
+                            np.concatenate([inst1000.trans, ext.trans]), np.concatenate([inst1000.scale, ext.scale]))
+    return {100: scenes.subset(inst1000, np.arange(100)), 1000: inst1000, 5000: five}
+
+
+def mix_requests(n, seed, n_assets_offset=0, inst_sets=None):
+    """n requests drawn from config 5's mix: scene size, resolution, tau and walk frame."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        out.append((int(rng.choice([100, 1000, 5000])), MIX_RES[int(rng.integers(0, 3))],
+                    float(MIX_TAUS[int(rng.integers(0, 4))]), int(rng.integers(0, 300))))
+    return out
+
+
+def serve_mix_leg(ctx, scenes_fp32, scenes_fp16, slots, tuned, seconds, max_outstanding=64, rates=MIX_RATES):
+    """Config 5: Poisson arrivals at each rate for `seconds`, each request drawn from the mix
+    (100 / 1000 / 5000 instances, 720p / 1080p / 4K, tau 0.5-4 px, a walk frame), images back into
+    pinned host memory.  served: `slots` slots, FP16 colour, autotuned blend, same-size requests
+    that wait together rendered as one frame; plain: one slot, FP32 attributes, one request per
+    frame, default blend (serial plain rendering of the same stream).  A client keeps at most
+    max_outstanding requests in flight (host output buffers) and drops arrivals beyond that
+    (counted).  Latency = submit -> done on the server's clock."""
+    from paper_2505_06523_gb300 import _native as N
+    from synth import scenes
+    cams = {}
+
+    def cam_of(res, f):
+        if (res, f) not in cams:
+            cams[(res, f)] = scenes.crowd_camera(f, res[0], res[1])
+        return cams[(res, f)]
+
+    out = {"seconds_per_rate": seconds, "max_outstanding": max_outstanding, "slots": slots, "rates": []}
+    arms = {"plain": (1, 1, scenes_fp32, DEFAULT_BLEND), "served": (slots, 8, scenes_fp16, tuned)}
+    rng = np.random.default_rng(3000)
+    for rate in rates:
+        n = max(1, int(round(rate * seconds)))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        reqs = mix_requests(n, seed=int(rate))
+        row = {"rate": rate, "requests": n}
+        for name, (k, merge, sc, bopts) in arms.items():
+            _blend_options(ctx, bopts)
+            ctx.set_option(N.V3DG_OPT_SERVE_MERGE, merge)
+            ctx.server_start(k)
+            for (ni, res, tau, f) in reqs[:2 * k]:   # slots grow their buffers
+                _wait(ctx, ctx.submit(sc[ni], cam_of(res, f), tau))
+            pending, lat, dropped, failed, views = [], [], 0, {}, []
+            t0 = time.perf_counter()
+            i = 0
+            while i < n or pending:
+                now = time.perf_counter() - t0
+                while i < n and arrivals[i] <= now:
+                    if len(pending) < max_outstanding:
+                        ni, res, tau, f = reqs[i]
+                        pending.append(ctx.submit(sc[ni], cam_of(res, f), tau))
+                    else:
+                        dropped += 1
+                    i += 1
+                still = []
+                for t in pending:
+                    try:
+                        r = ctx.poll(t, 0)
+                    except N.V3dgError as e:   # a failed request: counted by its status, not timed
+                        key = N.STATUS_NAMES[e.status] if 0 <= e.status < len(N.STATUS_NAMES) else str(e.status)
+                        failed[key] = failed.get(key, 0) + 1
+                        continue
+                    if r is None:
+                        still.append(t)
+                    else:
+                        lat.append(r[0]["done_ms"] - r[0]["submit_ms"])
+                        views.append(r[0]["batch_views"])
+                pending = still
+                if pending or i < n:
+                    time.sleep(0.0005)
+            wall = time.perf_counter() - t0
+            ctx.server_stop()
+            row[name] = {"completed": len(lat), "dropped": dropped, "failed": failed, "achieved": len(lat) / wall,
+                         "mean_views_per_frame": float(np.mean(views)) if views else 0.0, **_pcts(lat)}
+        out["rates"].append(row)
+    ctx.set_option(N.V3DG_OPT_SERVE_MERGE, 8)
+    _blend_options(ctx, DEFAULT_BLEND)
     return out
 
 

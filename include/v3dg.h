@@ -136,6 +136,13 @@ enum {
                                 warps that each own two pixel rows and walk only the records whose
                                 box spans them.  Variant 1 always blends whole tiles
                                 (V3DG_OPT_SPLIT_PAIRS is ignored). */
+  V3DG_OPT_SERVE_MERGE = 12,   /* server (read at v3dg_server_start): a slot that takes a request
+                                also takes up to this many - 1 queued requests with the same image
+                                size, intrinsics and near plane whose memory estimates fit the
+                                budget, and renders them as the views of one frame (each view its
+                                own scene, camera and tolerance; every stage one launch for all);
+                                each image is the one its request gives alone, bit for bit.  1..64,
+                                default 8; 1: one request per frame. */
   V3DG_OPT_GRAPHS = 10         /* 1: v3dg_select only stages the camera and instances, and
                                 v3dg_render runs the selection and the whole render as one CUDA
                                 graph, captured the first time a configuration (instance and view
@@ -253,6 +260,14 @@ v3dg_status v3dg_sort_pairs(v3dg_ctx* ctx, uint32_t* keys, uint32_t* vals, uint6
  * V3DG_ETIMEOUT.  Synchronous on the context's stream; the context stays usable either way. */
 v3dg_status v3dg_check_wait(v3dg_ctx* ctx, uint32_t spin_limit, int predecessor_publishes, uint32_t* prefix);
 
+/* Release the frame buffers of the context (render list, sort keys and values, records, pairs,
+ * images of v3dg_render_host, ...), which grow with the largest frame rendered and are otherwise
+ * kept for the next frames; they grow again on demand, and the next v3dg_render needs a new
+ * v3dg_select.  Device memory goes back to the context's allocator (or to cudaFree).  *released
+ * (may be NULL): the bytes released.  V3DG_EBUSY while a server runs.  The paper has no
+ * counterpart. */
+v3dg_status v3dg_release_buffers(v3dg_ctx* ctx, uint64_t* released);
+
 /* Largest n that v3dg_sort_pairs_noalloc accepts (its fixed scratch holds this many pairs). */
 #define V3DG_SORT_NOALLOC_MAX_PAIRS (1u << 20)
 
@@ -286,8 +301,12 @@ v3dg_status v3dg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, uint64_t n, 
  * requests in flight plus its own fit `hbm_budget` bytes (0: no limit; a request is always
  * admitted when none is in flight), so requests overlap on the GPU as soon as they arrive.  A
  * request that starts while no other one is in flight runs on a high-priority stream, the others
- * on low-priority streams, so a frame alone keeps its solo latency and later ones fill idle SMs.  Each frame is checked and re-run with
- * larger buffers on overflow, as v3dg_render does with V3DG_OPT_SYNC_CHECK.  While a server runs,
+ * on low-priority streams, so a frame alone keeps its solo latency and later ones fill idle SMs.
+ * Each frame is checked and re-run with larger buffers on overflow, as v3dg_render does with
+ * V3DG_OPT_SYNC_CHECK.  Device memory: a slot that holds more frame buffers than its share of the
+ * budget (or, with no budget, of 3/4 of the device memory free at start) releases them after its
+ * request; a request that runs out of device memory beside others is rendered again once no other
+ * request is on the GPU (new requests wait meanwhile), and fails with V3DG_ENOMEM only alone.  While a server runs,
  * v3dg_set_option and v3dg_load_hierarchy return V3DG_EBUSY.  Status EBUSY if a server already
  * runs, ENOTFOUND if no asset is loaded. */
 v3dg_status v3dg_server_start(v3dg_ctx* ctx, int slots, uint64_t hbm_budget);
@@ -316,11 +335,11 @@ typedef struct {
 
 /* Completion record.  Times are milliseconds on the server's steady clock since it started. */
 typedef struct {
-  v3dg_status status;  /* the frame's own status (V3DG_OK, V3DG_ETIMEOUT, V3DG_ECUDA, ...) */
-  uint32_t reserved;
+  v3dg_status status;    /* the frame's own status (V3DG_OK, V3DG_ETIMEOUT, V3DG_ECUDA, ...) */
+  uint32_t batch_views;  /* requests rendered together in this request's frame (V3DG_OPT_SERVE_MERGE) */
   double submit_ms, start_ms, done_ms;
-  uint64_t visible;    /* visible Gaussians of the frame */
-  uint64_t pairs;      /* (tile, Gaussian) pairs of the frame */
+  uint64_t visible;      /* visible Gaussians of the frame (of all its views when batch_views > 1) */
+  uint64_t pairs;        /* (tile, Gaussian) pairs of the frame (likewise) */
 } v3dg_result;
 
 /* Queue a request; *ticket receives its id (1, 2, ...).  Validation errors are returned here

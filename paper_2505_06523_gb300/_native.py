@@ -26,6 +26,7 @@ V3DG_OPT_SELECT_TOPDOWN = 8
 V3DG_OPT_BLEND_BATCH = 9
 V3DG_OPT_GRAPHS = 10
 V3DG_OPT_BLEND_MODE = 11
+V3DG_OPT_SERVE_MERGE = 12
 
 
 class V3dgError(RuntimeError):
@@ -73,7 +74,7 @@ class v3dg_request(ctypes.Structure):
 
 
 class v3dg_result(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_uint32), ("submit_ms", ctypes.c_double),
+    _fields_ = [("status", ctypes.c_int32), ("batch_views", ctypes.c_uint32), ("submit_ms", ctypes.c_double),
                 ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double), ("visible", ctypes.c_uint64),
                 ("pairs", ctypes.c_uint64)]
 
@@ -108,6 +109,7 @@ SIGNATURES = {
     "v3dg_sort_pairs": (_I32, [_P, _P, _P, _U64, _I32, _I32]),
     "v3dg_sort_pairs_noalloc": (_I32, [_P, _P, _U64, _I32, _I32, _P]),
     "v3dg_check_wait": (_I32, [_P, _U32, _I32, ctypes.POINTER(_U32)]),
+    "v3dg_release_buffers": (_I32, [_P, ctypes.POINTER(_U64)]),
     "v3dg_server_start": (_I32, [_P, _I32, _U64]),
     "v3dg_server_stop": (_I32, [_P]),
     "v3dg_submit": (_I32, [_P, ctypes.POINTER(v3dg_request), ctypes.POINTER(_U64)]),
@@ -255,6 +257,12 @@ def v3dg_check_wait(ctx, spin_limit: int, predecessor_publishes: bool) -> int:
     p = _U32()
     _check(ctx, lib().v3dg_check_wait(ctx, spin_limit, 1 if predecessor_publishes else 0, ctypes.byref(p)))
     return p.value
+
+
+def v3dg_release_buffers(ctx) -> int:
+    b = _U64()
+    _check(ctx, lib().v3dg_release_buffers(ctx, ctypes.byref(b)))
+    return b.value
 
 
 def v3dg_server_start(ctx, slots: int, hbm_budget: int = 0) -> None:

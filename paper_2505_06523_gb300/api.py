@@ -210,6 +210,11 @@ class Context:
         m, b, sp, ms = N.v3dg_autotune_blend(self.ctx)
         return {"mode": m, "batch": b, "split_pairs": sp, "ms": ms}
 
+    def release_buffers(self) -> int:
+        """Release the frame buffers (v3dg_release_buffers); returns the bytes released.  PyTorch's
+        caching allocator keeps the blocks until torch.cuda.empty_cache()."""
+        return N.v3dg_release_buffers(self.ctx)
+
     def check_wait(self, spin_limit: int, predecessor_publishes: bool) -> int:
         """The bounded-wait diagnostic (v3dg_check_wait); raises V3dgError(V3DG_ETIMEOUT) when the
         look-back gives up."""

@@ -30,7 +30,7 @@ constexpr uint32_t kExpWarps = kExpThreads / 32;
 // contiguous.
 __global__ void __launch_bounds__(kExpThreads)
 k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uint32_t cap, uint32_t cap_pairs,
-         int tiles_x, const uint2* __restrict__ list, uint32_t inst_per_view, uint32_t tiles_per_view,
+         int tiles_x, const uint2* __restrict__ list, const InstFrame* __restrict__ inst_views, uint32_t tiles_per_view,
          uint32_t* __restrict__ pk, uint32_t* __restrict__ pv, uint32_t* __restrict__ frame, uint32_t tc_slot,
          uint64_t* __restrict__ status, uint32_t epoch) {
   __shared__ uint32_t s_off[kExpTile + 1];
@@ -59,7 +59,7 @@ k_expand(const uint32_t* __restrict__ slots, const uint2* __restrict__ rect, uin
       const uint2 r = rect[slot];
       s_slot[j] = slot;
       s_rect[j] = r;
-      s_tbase[j] = inst_per_view ? (list[slot / kSlots].x / inst_per_view) * tiles_per_view : 0u;
+      s_tbase[j] = inst_views ? inst_views[list[slot / kSlots].x].view * tiles_per_view : 0u;
       c[i] = rect_area(r);
     }
     sum += c[i];
@@ -180,13 +180,13 @@ k_ranges(const uint32_t* __restrict__ tk, uint32_t cap_pairs, const uint32_t* __
 }  // namespace
 
 cudaError_t launch_expand(const uint32_t* slots, const uint2* rect, uint32_t cap, uint32_t cap_pairs, int tiles_x,
-                          const uint2* list, uint32_t inst_per_view, uint32_t tiles_per_view, uint32_t* pk,
+                          const uint2* list, const InstFrame* inst_views, uint32_t tiles_per_view, uint32_t* pk,
                           uint32_t* pv, uint32_t* frame, uint32_t tc_slot, uint64_t* status, uint32_t epoch,
                           int sm_count, cudaStream_t st) {
   // persistent grid: at most the resident blocks (8 of 256 threads per SM), whatever the capacity
   const uint32_t blocks = std::min<uint32_t>((cap + kExpTile - 1) / kExpTile, uint32_t(sm_count) * 8u);
   if (blocks)
-    k_expand<<<blocks, kExpThreads, 0, st>>>(slots, rect, cap, cap_pairs, tiles_x, list, inst_per_view, tiles_per_view,
+    k_expand<<<blocks, kExpThreads, 0, st>>>(slots, rect, cap, cap_pairs, tiles_x, list, inst_views, tiles_per_view,
                                              pk, pv, frame, tc_slot, status, epoch);
   k_pairs_eff<<<1, 1, 0, st>>>(frame, cap_pairs);
   return cudaGetLastError();

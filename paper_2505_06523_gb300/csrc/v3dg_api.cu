@@ -69,6 +69,7 @@ struct Pipe {
 
   std::vector<uint32_t> inst_asset;
   std::vector<double> inst_rot, inst_trans, inst_scale;
+  std::vector<uint32_t> frame_asset;   // asset of each instance frame of the current selection
 
   bool selected = false, rendered = false;
   v3dg_camera cam{};
@@ -118,6 +119,7 @@ struct v3dg_ctx {
   int topdown = 2;          // 0 flat, 1 level by level from the roots (same cut), 2 top-down for large scenes
   int blend_batch = 512;    // records staged per blend batch: 128, 256 or 512
   int blend_mode = 0;       // 0: two-phase blend; 1: bulk-copy staging, warps composite row pairs
+  int serve_merge = 8;      // server: most queued requests of one image geometry rendered together
   bool graphs = false;      // capture each frame's launches once and replay them as a CUDA graph
   Pipe main;
   Server* server = nullptr;
@@ -263,31 +265,46 @@ v3dg_status check_camera(Pipe* c, const v3dg_camera* cam) {
   return V3DG_OK;
 }
 
-// Per-frame set-up of n_views cameras (same intrinsics, image size and near plane) over the
-// pipe's instances: instance frame v * n + i holds M = W_v [s R | t] of instance i.
-v3dg_status setup_frame(Pipe* c, const v3dg_camera* cams, uint32_t n_views, float tau_px) {
-  if (!cams || n_views == 0) return fail(c, V3DG_EINVAL, "no camera");
+// One view of a frame: its camera, tolerance and instances (host arrays, FP64).
+struct ViewSpec {
+  const v3dg_camera* cam = nullptr;
+  float tau_px = 0.f;
+  uint32_t n = 0;
+  const uint32_t* asset = nullptr;
+  const double* rot = nullptr;
+  const double* trans = nullptr;
+  const double* scale = nullptr;
+};
+
+// Per-frame set-up of n_views views that share image size, intrinsics and near plane; each has
+// its own camera, tolerance and instances.  The instance frames are the views' instances one view
+// after the other, each carrying M = W_v [s R | t], its view id and its tau_F.
+v3dg_status setup_views(Pipe* c, const ViewSpec* views, uint32_t n_views) {
+  if (!views || n_views == 0) return fail(c, V3DG_EINVAL, "no camera");
+  uint64_t nf64 = 0;
   for (uint32_t v = 0; v < n_views; ++v) {
-    ST(check_camera(c, cams + v));
-    const v3dg_camera& a = cams[0];
-    const v3dg_camera& b = cams[v];
+    ST(check_camera(c, views[v].cam));
+    const v3dg_camera& a = *views[0].cam;
+    const v3dg_camera& b = *views[v].cam;
     if (b.width != a.width || b.height != a.height || b.fx != a.fx || b.fy != a.fy || b.cx != a.cx || b.cy != a.cy ||
         b.near_z != a.near_z)
       return fail(c, V3DG_EINVAL, "camera %u differs from camera 0 in image size, intrinsics or near plane", v);
+    if (!(views[v].tau_px >= 0.f) || !std::isfinite(views[v].tau_px))
+      return fail(c, V3DG_EINVAL, "tau_px must be finite and >= 0");
+    nf64 += views[v].n;
   }
-  const v3dg_camera* cam = cams;
-  if (!(tau_px >= 0.f) || !std::isfinite(tau_px)) return fail(c, V3DG_EINVAL, "tau_px must be finite and >= 0");
+  const v3dg_camera* cam = views[0].cam;
   if (c->ctx->assets.empty()) return fail(c, V3DG_ENOTFOUND, "no hierarchy loaded");
   const uint64_t tiles = uint64_t((cam->width + kTile - 1) / kTile) * uint64_t((cam->height + kTile - 1) / kTile);
   if (tiles * n_views > uint64_t(kMaxTiles))
     return fail(c, V3DG_EINVAL, "image too large (%llu tiles of 16x16 over %u views, at most %d)",
                 (unsigned long long)(tiles * n_views), n_views, kMaxTiles);
-  if (uint64_t(c->inst_asset.size()) * n_views > 0xFFFFFFFull) return fail(c, V3DG_EINVAL, "too many instance views");
-  const uint32_t n = uint32_t(c->inst_asset.size());
+  if (nf64 > 0xFFFFFFFull) return fail(c, V3DG_EINVAL, "too many instance views");
+  const uint32_t nf = uint32_t(nf64);
 
   c->cam = *cam;
   if (!(c->cam.near_z > 0.f)) c->cam.near_z = 0.01f;
-  c->tau_px = tau_px;
+  c->tau_px = views[0].tau_px;
   CamConst& k = c->cc;
   k.fx = cam->fx; k.fy = cam->fy; k.cx = cam->cx; k.cy = cam->cy;
   k.near_z = c->cam.near_z;
@@ -305,13 +322,14 @@ v3dg_status setup_frame(Pipe* c, const v3dg_camera* cams, uint32_t n_views, floa
   uint32_t max_nodes = 0;
   for (auto& a : c->ctx->assets) max_nodes = std::max(max_nodes, a.n_nodes);
   c->node_blocks = int((max_nodes + 2047) / 2048);   // k_select covers 2048 nodes per block
-  c->n_inst_frame = n * n_views;
+  c->n_inst_frame = nf;
   c->n_views = n_views;
+  c->frame_asset.resize(nf);
   // the projection is specialised for the colour formats of the assets this frame draws
   c->color_formats = 0;
-  for (uint32_t a : c->inst_asset) c->color_formats |= c->ctx->assets[a].half_color ? 2 : 1;
+  for (uint32_t v = 0; v < n_views; ++v)
+    for (uint32_t i = 0; i < views[v].n; ++i) c->color_formats |= c->ctx->assets[views[v].asset[i]].half_color ? 2 : 1;
   if (!c->color_formats) c->color_formats = 1;
-  const uint32_t nf = n * n_views;
 
   // the pinned staging buffer is reused: wait until the previous upload out of it has completed
   if (c->ev_inst) CU(cudaEventSynchronize(c->ev_inst));
@@ -324,16 +342,18 @@ v3dg_status setup_frame(Pipe* c, const v3dg_camera* cams, uint32_t n_views, floa
   }
   ST(ensure(c, c->d_inst, sizeof(InstFrame) * std::max<uint32_t>(nf, 1)));
 
+  uint32_t fi = 0;
   for (uint32_t v = 0; v < n_views; ++v) {
-    const double* W = cams[v].world_to_cam;
+    const ViewSpec& vs = views[v];
+    const double* W = vs.cam->world_to_cam;
     double C[3];  // camera centre -R_w^T t_w
     for (int j = 0; j < 3; ++j) C[j] = -((W[0 * 4 + j] * W[3] + W[1 * 4 + j] * W[7]) + W[2 * 4 + j] * W[11]);
-    for (uint32_t i = 0; i < n; ++i) {
-      InstFrame& f = c->h_inst[size_t(v) * n + i];
+    for (uint32_t i = 0; i < vs.n; ++i, ++fi) {
+      InstFrame& f = c->h_inst[fi];
       std::memset(&f, 0, sizeof f);
-      const double* R = &c->inst_rot[9 * size_t(i)];
-      const double* t = &c->inst_trans[3 * size_t(i)];
-      const double s = c->inst_scale[i];
+      const double* R = &vs.rot[9 * size_t(i)];
+      const double* t = &vs.trans[3 * size_t(i)];
+      const double s = vs.scale[i];
       double A[9];
       for (int q = 0; q < 9; ++q) A[q] = s * R[q];
       for (int r = 0; r < 3; ++r) {
@@ -348,15 +368,34 @@ v3dg_status setup_frame(Pipe* c, const v3dg_camera* cams, uint32_t n_views, floa
       }
       f.s = float(s);
       f.s64 = s;
-      const uint32_t a = c->inst_asset[i];
+      const uint32_t a = vs.asset[i];
       f.asset = a;
-      f.tau_f = float(double(c->ctx->assets[a].gpg) * double(tau_px) * double(tau_px));
+      f.view = v;
+      f.tau_f = float(double(c->ctx->assets[a].gpg) * double(vs.tau_px) * double(vs.tau_px));
+      c->frame_asset[fi] = a;
     }
   }
   if (nf) CU(cudaMemcpyAsync(c->d_inst.p, c->h_inst, sizeof(InstFrame) * nf, cudaMemcpyHostToDevice, c->stream));
   if (!c->ev_inst) CU(cudaEventCreateWithFlags(&c->ev_inst, cudaEventDisableTiming));
   CU(cudaEventRecord(c->ev_inst, c->stream));
   return V3DG_OK;
+}
+
+// Per-frame set-up of n_views cameras (same intrinsics, image size and near plane) over the
+// pipe's instances: instance frame v * n + i holds M = W_v [s R | t] of instance i.
+v3dg_status setup_frame(Pipe* c, const v3dg_camera* cams, uint32_t n_views, float tau_px) {
+  if (!cams || n_views == 0) return fail(c, V3DG_EINVAL, "no camera");
+  std::vector<ViewSpec> vs(n_views);
+  for (uint32_t v = 0; v < n_views; ++v) {
+    vs[v].cam = cams + v;
+    vs[v].tau_px = tau_px;
+    vs[v].n = uint32_t(c->inst_asset.size());
+    vs[v].asset = c->inst_asset.data();
+    vs[v].rot = c->inst_rot.data();
+    vs[v].trans = c->inst_trans.data();
+    vs[v].scale = c->inst_scale.data();
+  }
+  return setup_views(c, vs.data(), n_views);
 }
 
 // Buffers of the top-down selection for the current instances: two frontiers that can each hold
@@ -461,7 +500,7 @@ v3dg_status enqueue_render(Pipe* c, float* rgb, float* t_out) {
   stage_event(c, kStageBin);
   const int tiles_view = k.tiles_x * k.tiles_y;
   CU(launch_expand(dslots, P<uint2>(c->d_rect), c->cap_slots, c->cap_pairs, k.tiles_x, P<uint2>(c->d_list),
-                   c->n_views > 1 ? c->n_inst_frame / c->n_views : 0u, uint32_t(tiles_view), P<uint32_t>(c->d_pk0),
+                   c->n_views > 1 ? P<InstFrame>(c->d_inst) : nullptr, uint32_t(tiles_view), P<uint32_t>(c->d_pk0),
                    P<uint32_t>(c->d_pv0), frame, 1, P<uint64_t>(c->d_status), next_epoch(c), sm, c->stream));
   c->ctx->launches += 2;
 
@@ -744,6 +783,38 @@ void pipe_free(Pipe* c) {
   for (auto& e : c->ev) e = nullptr;
 }
 
+// The frame buffers a pipe holds (they grow with the largest frame it has rendered).
+DevBuf* const* frame_buffers(Pipe* c, size_t* n) {
+  static thread_local DevBuf* bs[24];
+  DevBuf* list[] = {&c->d_list, &c->d_ref, &c->d_keys0, &c->d_keys1, &c->d_vals0, &c->d_vals1, &c->d_rec,
+                    &c->d_rect, &c->d_pk0, &c->d_pk1, &c->d_pv0, &c->d_pv1, &c->d_ranges, &c->d_status,
+                    &c->d_cut, &c->d_img, &c->d_timg, &c->d_sort_k, &c->d_sort_v, &c->d_order, &c->d_front0,
+                    &c->d_front1, &c->d_bitmap};
+  *n = sizeof(list) / sizeof(list[0]);
+  for (size_t i = 0; i < *n; ++i) bs[i] = list[i];
+  return bs;
+}
+
+uint64_t pipe_bytes(Pipe* c) {
+  size_t n = 0;
+  DevBuf* const* bs = frame_buffers(c, &n);
+  uint64_t t = 0;
+  for (size_t i = 0; i < n; ++i) t += bs[i]->bytes;
+  return t;
+}
+
+// Releases the frame buffers (after the pipe's stream has finished with them); capacities start
+// over and grow again on demand.  A captured frame graph refers to them, so it is dropped.
+void pipe_trim(Pipe* c) {
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  size_t n = 0;
+  DevBuf* const* bs = frame_buffers(c, &n);
+  for (size_t i = 0; i < n; ++i) dfree(c, *bs[i]);
+  c->cap_nodes = c->cap_pairs = c->cap_slots = c->status_words = c->cap_cut = 0;
+  c->selected = c->rendered = false;
+}
+
 // ------------------------------------------------------------------ serving
 
 // One queued request: a copy of its scene and camera, where its image goes, and its admission
@@ -765,6 +836,7 @@ struct Finished {
   v3dg_status status = V3DG_OK;
   double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
   uint64_t visible = 0, pairs = 0;
+  uint32_t batch_views = 1;
 };
 
 }  // namespace
@@ -779,6 +851,8 @@ struct Finished {
 struct Server {
   v3dg_ctx* ctx = nullptr;
   uint64_t budget = 0;
+  size_t merge = 1;   // most requests rendered together as the views of one frame
+  uint64_t slot_keep = ~uint64_t(0);   // a slot holding more frame-buffer bytes than this releases them
   std::vector<std::unique_ptr<Pipe>> slots;
   std::vector<cudaStream_t> hi, lo;   // per slot: high- and low-priority streams
   std::vector<std::thread> threads;
@@ -787,7 +861,8 @@ struct Server {
   std::deque<Request> queue;
   std::unordered_map<uint64_t, Finished> finished;
   std::unordered_set<uint64_t> pending;   // issued and not yet reported by v3dg_poll
-  uint64_t next_ticket = 1, in_flight = 0, active = 0;
+  uint64_t next_ticket = 1, in_flight = 0, active = 0, waiting_alone = 0;
+  bool alone_busy = false;   // a slot renders requests alone after running out of device memory
   bool stop = false;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   double now_ms() const {
@@ -803,62 +878,147 @@ uint64_t request_bytes(uint32_t n_inst, const v3dg_camera& cam) {
   return uint64_t(cam.width) * uint64_t(cam.height) * 64u + uint64_t(n_inst) * (64u << 10);
 }
 
-v3dg_status run_request(Pipe* c, Request& rq, Finished* f) {
-  c->inst_asset.swap(rq.asset);
-  c->inst_rot.swap(rq.rot);
-  c->inst_trans.swap(rq.trans);
-  c->inst_scale.swap(rq.scale);
-  ST(setup_frame(c, &rq.cam, 1, rq.tau_px));
+constexpr uint64_t kMergePixels = 3840ull * 2160ull;   // pixels of a merged frame (all its views)
+constexpr uint64_t kMergeFrames = 8192;                // instance frames of a merged frame
+
+// Whether two requests can share one launch per stage: the same image size, intrinsics and near
+// plane (each keeps its own camera pose, scene and tolerance).
+bool same_geometry(const v3dg_camera& a, const v3dg_camera& b) {
+  return a.width == b.width && a.height == b.height && a.fx == b.fx && a.fy == b.fy && a.cx == b.cx &&
+         a.cy == b.cy && a.near_z == b.near_z;
+}
+
+// Renders the requests as the views of one frame (each view its own instances, camera and tau;
+// every stage one launch for all of them) and writes each view's image to its request's output.
+// Every view's image is the one its request gives alone, bit for bit.
+v3dg_status run_requests(Pipe* c, std::vector<Request>& rqs, Finished* f) {
+  const uint32_t nv = uint32_t(rqs.size());
+  std::vector<ViewSpec> vs(nv);
+  for (uint32_t v = 0; v < nv; ++v) {
+    Request& rq = rqs[v];
+    vs[v].cam = &rq.cam;
+    vs[v].tau_px = rq.tau_px;
+    vs[v].n = uint32_t(rq.asset.size());
+    vs[v].asset = rq.asset.data();
+    vs[v].rot = rq.rot.data();
+    vs[v].trans = rq.trans.data();
+    vs[v].scale = rq.scale.data();
+  }
+  ST(setup_views(c, vs.data(), nv));
   ST(enqueue_select(c));
   c->selected = true;
   c->rendered = false;
-  const size_t px = size_t(rq.cam.width) * size_t(rq.cam.height);
-  float* rgb = rq.rgb;
-  float* t = rq.t;
-  if (!rq.out_device) {
-    ST(ensure(c, c->d_img, sizeof(float) * 3 * px));
-    if (t) ST(ensure(c, c->d_timg, sizeof(float) * px));
+  const v3dg_camera& cam = rqs[0].cam;
+  const size_t px = size_t(cam.width) * size_t(cam.height);
+  bool any_t = false;
+  for (const Request& rq : rqs) any_t |= rq.t != nullptr;
+  float* rgb = nullptr;
+  float* t = nullptr;
+  if (nv == 1 && rqs[0].out_device) {   // one device request renders in place
+    rgb = rqs[0].rgb;
+    t = rqs[0].t;
+  } else {
+    ST(ensure(c, c->d_img, sizeof(float) * 3 * px * nv));
+    if (any_t) ST(ensure(c, c->d_timg, sizeof(float) * px * nv));
     rgb = P<float>(c->d_img);
-    t = t ? P<float>(c->d_timg) : nullptr;
+    t = any_t ? P<float>(c->d_timg) : nullptr;
   }
   ST(run_frame(c, rgb, t, true));
-  if (!rq.out_device) {
-    CU(cudaMemcpyAsync(rq.rgb, c->d_img.p, sizeof(float) * 3 * px, cudaMemcpyDeviceToHost, c->stream));
-    if (rq.t) CU(cudaMemcpyAsync(rq.t, c->d_timg.p, sizeof(float) * px, cudaMemcpyDeviceToHost, c->stream));
+  if (!(nv == 1 && rqs[0].out_device)) {
+    for (uint32_t v = 0; v < nv; ++v) {
+      const Request& rq = rqs[v];
+      const cudaMemcpyKind kind = rq.out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+      CU(cudaMemcpyAsync(rq.rgb, P<float>(c->d_img) + 3 * px * v, sizeof(float) * 3 * px, kind, c->stream));
+      if (rq.t) CU(cudaMemcpyAsync(rq.t, P<float>(c->d_timg) + px * v, sizeof(float) * px, kind, c->stream));
+    }
   }
   CU(cudaStreamSynchronize(c->stream));
   f->visible = c->h_frame[kVisible];
   f->pairs = c->h_frame[kPairs];
+  f->batch_views = nv;
   return V3DG_OK;
 }
 
+// A slot takes the request at the head of the queue and, if more are waiting, up to merge - 1
+// later ones with the same image geometry whose device-memory estimates still fit the budget;
+// they run as the views of one frame.
 void slot_main(Server* sv, Pipe* p, size_t slot) {
   cudaSetDevice(sv->ctx->device);
   for (;;) {
-    Request rq;
+    std::vector<Request> rqs;
+    uint64_t est = 0;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       sv->cv_work.wait(lk, [&] {
         if (sv->queue.empty()) return sv->stop;
+        if (sv->waiting_alone || sv->alone_busy) return false;   // a slot waits for or has its turn alone
         return sv->active == 0 || sv->in_flight + sv->queue.front().est_bytes <= sv->budget;
       });
       if (sv->queue.empty()) return;   // stopping and nothing left
-      rq = std::move(sv->queue.front());
+      rqs.push_back(std::move(sv->queue.front()));
       sv->queue.pop_front();
-      sv->in_flight += rq.est_bytes;
+      est = rqs[0].est_bytes;
+      const uint64_t tiles = uint64_t((rqs[0].cam.width + kTile - 1) / kTile) * uint64_t((rqs[0].cam.height + kTile - 1) / kTile);
+      const uint64_t px = uint64_t(rqs[0].cam.width) * uint64_t(rqs[0].cam.height);
+      uint64_t frames = rqs[0].asset.size();
+      // a merged frame stays within about one 4K frame of pixels and 8192 instance frames, so that
+      // its pairs and buffers stay within what one large request needs
+      for (auto it = sv->queue.begin(); it != sv->queue.end() && rqs.size() < sv->merge;) {
+        const bool fit = same_geometry(it->cam, rqs[0].cam) && sv->in_flight + est + it->est_bytes <= sv->budget &&
+                         tiles * (rqs.size() + 1) <= uint64_t(kMaxTiles) && px * (rqs.size() + 1) <= kMergePixels &&
+                         frames + it->asset.size() <= kMergeFrames;
+        if (fit) {
+          est += it->est_bytes;
+          frames += it->asset.size();
+          rqs.push_back(std::move(*it));
+          it = sv->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
+      sv->in_flight += est;
       p->stream = sv->active == 0 ? sv->hi[slot] : sv->lo[slot];   // the previous frame of this slot has completed
       ++sv->active;
     }
     Finished f;
-    f.t_submit = rq.t_submit;
+    bool alone = false;
     f.t_start = sv->now_ms();
-    f.status = run_request(p, rq, &f);
+    f.status = run_requests(p, rqs, &f);
+    if (f.status == V3DG_ENOMEM || (f.status == V3DG_EOVERFLOW && rqs.size() > 1)) {
+      // out of device memory beside the other frames in flight (or a merged frame beyond the
+      // buffer limits): release this slot's buffers, wait until no other request is on the GPU,
+      // and render the requests again one at a time
+      pipe_trim(p);
+      cudaGetLastError();
+      {   // every slot that holds requests is waiting, and none runs alone: take the turn
+        std::unique_lock<std::mutex> lk(sv->mu);
+        ++sv->waiting_alone;
+        sv->cv_done.wait(lk, [&] { return !sv->alone_busy && sv->active == sv->waiting_alone; });
+        --sv->waiting_alone;
+        sv->alone_busy = true;
+        alone = true;
+      }
+      f.status = V3DG_OK;
+      for (size_t r = 0; r < rqs.size() && f.status == V3DG_OK; ++r) {
+        std::vector<Request> one(1);
+        one[0] = std::move(rqs[r]);
+        f.status = run_requests(p, one, &f);
+        rqs[r] = std::move(one[0]);
+      }
+      f.batch_views = uint32_t(rqs.size());
+    }
+    if (f.status != V3DG_OK || pipe_bytes(p) > sv->slot_keep) pipe_trim(p);
     f.t_done = sv->now_ms();
     {
       std::lock_guard<std::mutex> lk(sv->mu);
-      sv->in_flight -= rq.est_bytes;
+      sv->in_flight -= est;
       --sv->active;
-      sv->finished[rq.ticket] = f;
+      if (alone) sv->alone_busy = false;
+      for (const Request& rq : rqs) {
+        Finished g = f;
+        g.t_submit = rq.t_submit;
+        sv->finished[rq.ticket] = g;
+      }
     }
     sv->cv_done.notify_all();
     sv->cv_work.notify_all();
@@ -965,6 +1125,10 @@ v3dg_status v3dg_set_option(v3dg_ctx* ctx, int option, int64_t value) {
     case V3DG_OPT_BLEND_BATCH:
       if (value != 128 && value != 256 && value != 512) return fail(c, V3DG_EINVAL, "blend batch must be 128, 256 or 512");
       ctx->blend_batch = int(value);
+      break;
+    case V3DG_OPT_SERVE_MERGE:
+      if (value < 1 || value > 64) return fail(c, V3DG_EINVAL, "requests per launch must be in [1, 64]");
+      ctx->serve_merge = int(value);
       break;
     case V3DG_OPT_BLEND_MODE:
       if (value != 0 && value != 1) return fail(c, V3DG_EINVAL, "blend mode must be 0 or 1");
@@ -1305,7 +1469,7 @@ v3dg_status v3dg_get_projected(v3dg_ctx* ctx, uint64_t cap, uint64_t* n, uint32_
     std::memcpy(&org, &r2.y, 4);
     const uint2 rr = rc[slot];
     if (inst) inst[q] = e.x;
-    if (local) local[q] = ctx->assets[c->inst_asset[e.x % c->inst_asset.size()]].node_first[e.y] + j;
+    if (local) local[q] = ctx->assets[c->frame_asset[e.x]].node_first[e.y] + j;
     if (u) {
       u[2 * q] = float(double(r0.x) + 16.0 * double(org & 0xFFFFu));
       u[2 * q + 1] = float(double(r0.y) + 16.0 * double(org >> 16));
@@ -1365,7 +1529,7 @@ v3dg_status v3dg_get_pairs(v3dg_ctx* ctx, uint64_t cap, uint64_t* n, uint32_t* t
     const uint2 e = list[slot / kSlots];
     if (depth_key) depth_key[q] = key_of[slot];
     if (inst) inst[q] = e.x;
-    if (local) local[q] = ctx->assets[c->inst_asset[e.x % c->inst_asset.size()]].node_first[e.y] + slot % kSlots;
+    if (local) local[q] = ctx->assets[c->frame_asset[e.x]].node_first[e.y] + slot % kSlots;
   }
   c->err.clear();
   return V3DG_OK;
@@ -1517,6 +1681,18 @@ v3dg_status v3dg_check_wait(v3dg_ctx* ctx, uint32_t spin_limit, int predecessor_
   return V3DG_OK;
 }
 
+v3dg_status v3dg_release_buffers(v3dg_ctx* ctx, uint64_t* released) {
+  Pipe* c = ctx ? &ctx->main : nullptr;
+  if (!c) return V3DG_EINVAL;
+  if (ctx->server) return fail(c, V3DG_EBUSY, "buffers cannot be released while a server runs");
+  CU(cudaSetDevice(ctx->device));
+  const uint64_t b = pipe_bytes(c);
+  pipe_trim(c);
+  if (released) *released = b;
+  c->err.clear();
+  return V3DG_OK;
+}
+
 v3dg_status v3dg_server_start(v3dg_ctx* ctx, int slots, uint64_t hbm_budget) {
   Pipe* c = ctx ? &ctx->main : nullptr;
   if (!c) return V3DG_EINVAL;
@@ -1528,6 +1704,16 @@ v3dg_status v3dg_server_start(v3dg_ctx* ctx, int slots, uint64_t hbm_budget) {
   if (!sv) return fail(c, V3DG_ENOMEM, "out of host memory");
   sv->ctx = ctx;
   sv->budget = hbm_budget ? hbm_budget : ~uint64_t(0);
+  sv->merge = size_t(ctx->serve_merge);
+  {  // each slot keeps at most its share of the budget (or of the free device memory) between requests
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    const uint64_t pool = hbm_budget ? hbm_budget : uint64_t(free_b) * 3 / 4;
+    if (pool) sv->slot_keep = pool / uint64_t(slots);
+  }
   int least = 0, greatest = 0;
   CU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
   for (int i = 0; i < slots; ++i) {
@@ -1622,6 +1808,7 @@ v3dg_status v3dg_poll(v3dg_ctx* ctx, uint64_t ticket, uint32_t timeout_us, v3dg_
   out->done_ms = f.t_done;
   out->visible = f.visible;
   out->pairs = f.pairs;
+  out->batch_views = f.batch_views;
   return V3DG_OK;
 }
 

@@ -55,7 +55,8 @@ struct alignas(16) InstFrame {
   double s64;
   float tau_f;             // area tolerance of this instance's asset
   uint32_t asset;
-  uint32_t pad[20];
+  uint32_t view;           // the camera (view) this instance frame belongs to
+  uint32_t pad[19];
 };
 static_assert(sizeof(InstFrame) == 256, "InstFrame layout");
 
@@ -172,10 +173,10 @@ cudaError_t blend_set_attributes();
 // Expansion of the depth-sorted visible Gaussians into (tile, slot) pairs in depth order; writes
 // frame[kPairs] (the total) and frame[kPairsEff] (0 if the frame overflowed).  rect: per slot,
 // the pixel box (x0 | x1 << 16, y0 | y1 << 16) of the alpha >= 1/255 ellipse, inclusive.
-// Several views: the render list's instance frames are view * inst_per_view + instance, and the
-// tile id of a pair is view * tiles_per_view + tile (inst_per_view 0: one view, list unused).
+// Several views: the tile id of a pair is view * tiles_per_view + tile, with the view of the
+// Gaussian's instance frame (inst_views[list[slot / 64].x].view; inst_views NULL: one view).
 cudaError_t launch_expand(const uint32_t* sorted_slots, const uint2* rect, uint32_t cap_slots, uint32_t cap_pairs,
-                          int tiles_x, const uint2* list, uint32_t inst_per_view, uint32_t tiles_per_view,
+                          int tiles_x, const uint2* list, const InstFrame* inst_views, uint32_t tiles_per_view,
                           uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* frame, uint32_t tile_counter_slot,
                           uint64_t* status, uint32_t epoch, int sm_count, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t* tile_keys, uint32_t cap_pairs, const uint32_t* frame,

@@ -83,9 +83,46 @@ def test_same_alone_and_in_the_mix(api, tiny_asset, small_asset, slots, budget):
         a_rgb, a_T, st = alone[k]
         assert rec["status"] == N.V3DG_OK
         assert rec["submit_ms"] <= rec["start_ms"] <= rec["done_ms"]
-        assert rec["visible"] == st["visible"] and rec["pairs"] == st["pairs"], k
+        if rec["batch_views"] == 1:   # merged frames report the counters of all their views
+            assert rec["visible"] == st["visible"] and rec["pairs"] == st["pairs"], k
         assert np.array_equal(rgb, a_rgb), k
         assert np.array_equal(T, a_T), k
+
+
+@pytest.mark.parametrize("merge", [8, 3])
+def test_merged_requests_equal_alone(api, tiny_asset, small_asset, merge):
+    """Requests of one image size that wait together are rendered as the views of one frame (each
+    its own instances, camera and tau); each image equals the one its request gives alone."""
+    Context, N = api
+    assets = [tiny_asset, small_asset]
+    crowd = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+    rng = np.random.default_rng(5)
+    reqs = []
+    for k in range(12):
+        idx = np.sort(rng.choice(200, size=[200, 30, 90, 1][k % 4], replace=False))
+        reqs.append((scenes.subset(crowd, idx), scenes.crowd_camera(int(rng.integers(0, 300)), width=240, height=136),
+                     [0.5, 1.0, 2.0, 4.0][k % 4]))
+    alone = _alone(Context, assets, reqs)
+    with Context(0) as ctx:
+        ctx.set_option(N.V3DG_OPT_SERVE_MERGE, merge)
+        for a in assets:
+            ctx.load_hierarchy(a)
+        ctx.server_start(1)
+        tickets = [ctx.submit(inst, cam, tau, want_T=True) for inst, cam, tau in reqs]
+        got = {}
+        while len(got) < len(tickets):
+            for t in tickets:
+                if t not in got:
+                    r = ctx.poll(t, 2000)
+                    if r is not None:
+                        got[t] = r
+        ctx.server_stop()
+    views = [got[t][0]["batch_views"] for t in tickets]
+    assert max(views) > 1 and max(views) <= merge, views
+    for k, t in enumerate(tickets):
+        rec, rgb, T = got[t]
+        assert rec["status"] == N.V3DG_OK
+        assert np.array_equal(rgb, alone[k][0]) and np.array_equal(T, alone[k][1]), (k, rec["batch_views"])
 
 
 def test_served_frame_matches_oracle(api, small_asset):
