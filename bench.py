@@ -656,12 +656,15 @@ def mix_requests(n, seed, n_assets_offset=0, inst_sets=None):
     return out
 
 
-def serve_mix_leg(ctx, scenes_fp32, scenes_fp16, slots, tuned, seconds, max_outstanding=64, rates=MIX_RATES):
-    """Config 5: Poisson arrivals at each rate for `seconds`, each request drawn from the mix
+def serve_mix_leg(ctx, scenes_fp32, scenes_fp16, slots, tuned, seconds, max_outstanding=64, rates=MIX_RATES,
+                  min_requests=500):
+    """Config 5: Poisson arrivals at each rate for `seconds` (and at least `min_requests` arrivals),
+    each request drawn from the mix
     (100 / 1000 / 5000 instances, 720p / 1080p / 4K, tau 0.5-4 px, a walk frame), images back into
-    pinned host memory.  served: `slots` slots, FP16 colour, autotuned blend, same-size requests
-    that wait together rendered as one frame; plain: one slot, FP32 attributes, one request per
-    frame, default blend (serial plain rendering of the same stream).  A client keeps at most
+    pinned host memory.  served: `slots` slots, FP16 colour, autotuned blend; served_merged: the
+    same, and up to 8 waiting requests of one image size rendered as one frame while requests pile
+    up; plain: one slot, FP32 attributes, one request per frame, default blend (serial plain
+    rendering of the same stream).  A client keeps at most
     max_outstanding requests in flight (host output buffers) and drops arrivals beyond that
     (counted).  Latency = submit -> done on the server's clock."""
     from paper_2505_06523_gb300 import _native as N
@@ -674,10 +677,11 @@ def serve_mix_leg(ctx, scenes_fp32, scenes_fp16, slots, tuned, seconds, max_outs
         return cams[(res, f)]
 
     out = {"seconds_per_rate": seconds, "max_outstanding": max_outstanding, "slots": slots, "rates": []}
-    arms = {"plain": (1, 1, scenes_fp32, DEFAULT_BLEND), "served": (slots, 8, scenes_fp16, tuned)}
+    arms = {"plain": (1, 1, scenes_fp32, DEFAULT_BLEND), "served": (slots, 1, scenes_fp16, tuned),
+            "served_merged": (slots, 8, scenes_fp16, tuned)}
     rng = np.random.default_rng(3000)
     for rate in rates:
-        n = max(1, int(round(rate * seconds)))
+        n = max(min_requests, int(round(rate * seconds)))   # arrivals at this rate (at least min_requests)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
         reqs = mix_requests(n, seed=int(rate))
         row = {"rate": rate, "requests": n}
@@ -688,6 +692,7 @@ def serve_mix_leg(ctx, scenes_fp32, scenes_fp16, slots, tuned, seconds, max_outs
             for (ni, res, tau, f) in reqs[:2 * k]:   # slots grow their buffers
                 _wait(ctx, ctx.submit(sc[ni], cam_of(res, f), tau))
             pending, lat, dropped, failed, views = [], [], 0, {}, []
+            cls_of, by_cls = {}, {}
             t0 = time.perf_counter()
             i = 0
             while i < n or pending:
@@ -695,7 +700,9 @@ def serve_mix_leg(ctx, scenes_fp32, scenes_fp16, slots, tuned, seconds, max_outs
                 while i < n and arrivals[i] <= now:
                     if len(pending) < max_outstanding:
                         ni, res, tau, f = reqs[i]
-                        pending.append(ctx.submit(sc[ni], cam_of(res, f), tau))
+                        t = ctx.submit(sc[ni], cam_of(res, f), tau)
+                        pending.append(t)
+                        cls_of[t] = f"{ni}@{res[1]}p"
                     else:
                         dropped += 1
                     i += 1
@@ -712,15 +719,17 @@ def serve_mix_leg(ctx, scenes_fp32, scenes_fp16, slots, tuned, seconds, max_outs
                     else:
                         lat.append(r[0]["done_ms"] - r[0]["submit_ms"])
                         views.append(r[0]["batch_views"])
+                        by_cls.setdefault(cls_of.pop(t, "?"), []).append(r[0]["done_ms"] - r[0]["start_ms"])
                 pending = still
                 if pending or i < n:
                     time.sleep(0.0005)
             wall = time.perf_counter() - t0
             ctx.server_stop()
             row[name] = {"completed": len(lat), "dropped": dropped, "failed": failed, "achieved": len(lat) / wall,
-                         "mean_views_per_frame": float(np.mean(views)) if views else 0.0, **_pcts(lat)}
+                         "mean_views_per_frame": float(np.mean(views)) if views else 0.0, **_pcts(lat),
+                         "service_ms_by_class": {k: round(float(np.mean(v)), 1) for k, v in sorted(by_cls.items())}}
         out["rates"].append(row)
-    ctx.set_option(N.V3DG_OPT_SERVE_MERGE, 8)
+    ctx.set_option(N.V3DG_OPT_SERVE_MERGE, 1)
     _blend_options(ctx, DEFAULT_BLEND)
     return out
 

@@ -141,8 +141,9 @@ enum {
                                 size, intrinsics and near plane whose memory estimates fit the
                                 budget, and renders them as the views of one frame (each view its
                                 own scene, camera and tolerance; every stage one launch for all);
-                                each image is the one its request gives alone, bit for bit.  1..64,
-                                default 8; 1: one request per frame. */
+                                each image is the one its request gives alone, bit for bit.  Only
+                                while at least as many requests wait as there are slots.  1..64,
+                                default 1 (one request per frame). */
   V3DG_OPT_GRAPHS = 10         /* 1: v3dg_select only stages the camera and instances, and
                                 v3dg_render runs the selection and the whole render as one CUDA
                                 graph, captured the first time a configuration (instance and view
@@ -298,15 +299,21 @@ v3dg_status v3dg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, uint64_t n, 
  * own streams and frame buffers (from cudaMalloc: the context's allocator is only ever called from
  * the thread that owns the context) and shares the loaded assets (load them all first).  Requests
  * wait in arrival order; a free worker takes the next one when the device-memory estimates of the
- * requests in flight plus its own fit `hbm_budget` bytes (0: no limit; a request is always
- * admitted when none is in flight), so requests overlap on the GPU as soon as they arrive.  A
+ * requests in flight plus its own fit `hbm_budget` bytes (0: 3/4 of the device memory free at
+ * start; a request is always admitted when none is in flight), so requests overlap on the GPU as
+ * soon as they arrive.  A request's estimate (also used to size its frame buffers before its
+ * first frame) grows with its instances, the square root of 1 / tau_px and, for its pairs, of its
+ * pixel count (about 9 MB per instance of a 1M-leaf crowd at 1920x1080, tau 1).  A request
+ * estimated above half its slot's share of the budget is heavy: it saturates the GPU on its own,
+ * so at most one heavy request is in flight (light ones still overlap it).  A
  * request that starts while no other one is in flight runs on a high-priority stream, the others
  * on low-priority streams, so a frame alone keeps its solo latency and later ones fill idle SMs.
  * Each frame is checked and re-run with larger buffers on overflow, as v3dg_render does with
- * V3DG_OPT_SYNC_CHECK.  Device memory: a slot that holds more frame buffers than its share of the
- * budget (or, with no budget, of 3/4 of the device memory free at start) releases them after its
- * request; a request that runs out of device memory beside others is rendered again once no other
- * request is on the GPU (new requests wait meanwhile), and fails with V3DG_ENOMEM only alone.  While a server runs,
+ * V3DG_OPT_SYNC_CHECK.  Device memory: the slots allocate from one stream-ordered pool of the
+ * server; a slot that holds more frame buffers than half its share of the budget releases them
+ * to the pool after its request; a request that runs out of device memory beside others is
+ * rendered again once no other request is on the GPU (new requests wait meanwhile), and fails
+ * with V3DG_ENOMEM only alone.  While a server runs,
  * v3dg_set_option and v3dg_load_hierarchy return V3DG_EBUSY.  Status EBUSY if a server already
  * runs, ENOTFOUND if no asset is loaded. */
 v3dg_status v3dg_server_start(v3dg_ctx* ctx, int slots, uint64_t hbm_budget);

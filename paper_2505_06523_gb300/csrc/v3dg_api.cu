@@ -66,6 +66,7 @@ struct Pipe {
   std::string err;
   cudaStream_t stream = nullptr;
   bool ctx_alloc = true;   // device memory from the context's allocator (else cudaMalloc)
+  cudaMemPool_t pool = nullptr;   // serving slots: stream-ordered allocations from the server's pool
 
   std::vector<uint32_t> inst_asset;
   std::vector<double> inst_rot, inst_trans, inst_scale;
@@ -119,7 +120,7 @@ struct v3dg_ctx {
   int topdown = 2;          // 0 flat, 1 level by level from the roots (same cut), 2 top-down for large scenes
   int blend_batch = 512;    // records staged per blend batch: 128, 256 or 512
   int blend_mode = 0;       // 0: two-phase blend; 1: bulk-copy staging, warps composite row pairs
-  int serve_merge = 8;      // server: most queued requests of one image geometry rendered together
+  int serve_merge = 1;      // server: most queued requests of one image geometry rendered together
   bool graphs = false;      // capture each frame's launches once and replay them as a CUDA graph
   Pipe main;
   Server* server = nullptr;
@@ -151,7 +152,9 @@ v3dg_status fail(Pipe* c, v3dg_status s, const char* fmt, ...) {
 
 void dfree(Pipe* c, DevBuf& b) {
   if (b.p) {
-    if (c->ctx->has_alloc && c->ctx_alloc)
+    if (c->pool)
+      cudaFreeAsync(b.p, c->stream);   // back to the server's pool, in stream order
+    else if (c->ctx->has_alloc && c->ctx_alloc)
       c->ctx->alloc.free(b.p, c->ctx->alloc.user);
     else
       cudaFree(b.p);
@@ -164,7 +167,13 @@ v3dg_status dalloc(Pipe* c, DevBuf& b, size_t bytes, bool zero = false) {
   if (bytes == 0) bytes = 256;
   bytes = (bytes + 255) & ~size_t(255);
   void* p = nullptr;
-  if (c->ctx->has_alloc && c->ctx_alloc) {
+  if (c->pool) {
+    const cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, c->pool, c->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, V3DG_ENOMEM, "pool allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+  } else if (c->ctx->has_alloc && c->ctx_alloc) {
     p = c->ctx->alloc.alloc(bytes, c->ctx->alloc.user);
     if (!p) return fail(c, V3DG_ENOMEM, "allocator returned NULL for %zu bytes", bytes);
   } else {
@@ -830,6 +839,7 @@ struct Request {
   bool out_device = false;
   uint64_t est_bytes = 0;
   double t_submit = 0.0;
+  bool heavy = false;   // estimated above its share of the budget: never beside another heavy one
 };
 
 struct Finished {
@@ -852,6 +862,7 @@ struct Server {
   v3dg_ctx* ctx = nullptr;
   uint64_t budget = 0;
   size_t merge = 1;   // most requests rendered together as the views of one frame
+  cudaMemPool_t pool = nullptr;   // the slots' frame buffers: freed memory is reused by any slot
   uint64_t slot_keep = ~uint64_t(0);   // a slot holding more frame-buffer bytes than this releases them
   std::vector<std::unique_ptr<Pipe>> slots;
   std::vector<cudaStream_t> hi, lo;   // per slot: high- and low-priority streams
@@ -861,7 +872,7 @@ struct Server {
   std::deque<Request> queue;
   std::unordered_map<uint64_t, Finished> finished;
   std::unordered_set<uint64_t> pending;   // issued and not yet reported by v3dg_poll
-  uint64_t next_ticket = 1, in_flight = 0, active = 0, waiting_alone = 0;
+  uint64_t next_ticket = 1, in_flight = 0, active = 0, waiting_alone = 0, heavy_active = 0;
   bool alone_busy = false;   // a slot renders requests alone after running out of device memory
   bool stop = false;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
@@ -874,8 +885,29 @@ namespace {
 
 // Admission estimate of a request's device memory: image and per-pixel buffers plus a share per
 // instance for its cut, records and pairs.
-uint64_t request_bytes(uint32_t n_inst, const v3dg_camera& cam) {
-  return uint64_t(cam.width) * uint64_t(cam.height) * 64u + uint64_t(n_inst) * (64u << 10);
+// Estimated frame size of a request, for admission and for sizing its buffers before the first
+// frame (so that it rarely overflows and re-runs): about 1,000 render-list clusters per instance of
+// a 1M-leaf crowd at tau 1 px (1.0M for the 1000-instance crowd at 1920x1080), growing with
+// sqrt(1 / tau) (a finer cut) and 25% headroom; pairs 2.25 per visible slot at 1920x1080, growing
+// with the square root of the pixel count (Gaussians span more tiles).  Bytes: per slot the depth
+// keys and values, record and box (72 B), per pair keys and values (16 B), per pixel 64 B.
+struct FrameEstimate {
+  uint64_t nodes, pairs, bytes;
+};
+
+FrameEstimate estimate_frame(uint32_t n_inst, const v3dg_camera& cam, float tau_px) {
+  const double px = double(cam.width) * double(cam.height);
+  const double nodes = 1250.0 * double(n_inst) * std::sqrt(1.0 / std::max(double(tau_px), 0.25));
+  const double pairs = nodes * 64.0 * 2.25 * std::sqrt(px / (1920.0 * 1080.0));
+  FrameEstimate e;
+  e.nodes = uint64_t(nodes);
+  e.pairs = uint64_t(pairs);
+  e.bytes = uint64_t(nodes * 64.0 * 72.0 + pairs * 16.0 + px * 64.0);
+  return e;
+}
+
+uint64_t request_bytes(uint32_t n_inst, const v3dg_camera& cam, float tau_px) {
+  return estimate_frame(n_inst, cam, tau_px).bytes;
 }
 
 constexpr uint64_t kMergePixels = 3840ull * 2160ull;   // pixels of a merged frame (all its views)
@@ -905,6 +937,15 @@ v3dg_status run_requests(Pipe* c, std::vector<Request>& rqs, Finished* f) {
     vs[v].scale = rq.scale.data();
   }
   ST(setup_views(c, vs.data(), nv));
+  // buffers sized from the requests' estimates before the first frame (they still grow on overflow)
+  uint64_t want_nodes = 0, want_pairs = 0;
+  for (const Request& rq : rqs) {
+    const FrameEstimate e = estimate_frame(uint32_t(rq.asset.size()), rq.cam, rq.tau_px);
+    want_nodes += e.nodes;
+    want_pairs += e.pairs;
+  }
+  c->cap_nodes = uint32_t(std::max<uint64_t>(c->cap_nodes, std::min<uint64_t>(want_nodes, kMaxNodes)));
+  c->cap_pairs = uint32_t(std::max<uint64_t>(c->cap_pairs, std::min<uint64_t>(want_pairs, kMaxPairs)));
   ST(enqueue_select(c));
   c->selected = true;
   c->rendered = false;
@@ -947,24 +988,32 @@ void slot_main(Server* sv, Pipe* p, size_t slot) {
   for (;;) {
     std::vector<Request> rqs;
     uint64_t est = 0;
+    bool heavy = false;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       sv->cv_work.wait(lk, [&] {
         if (sv->queue.empty()) return sv->stop;
         if (sv->waiting_alone || sv->alone_busy) return false;   // a slot waits for or has its turn alone
-        return sv->active == 0 || sv->in_flight + sv->queue.front().est_bytes <= sv->budget;
+        const Request& next = sv->queue.front();
+        if (sv->active == 0) return true;
+        if (next.heavy && sv->heavy_active) return false;   // large frames saturate the GPU on their own
+        return sv->in_flight + next.est_bytes <= sv->budget;
       });
       if (sv->queue.empty()) return;   // stopping and nothing left
       rqs.push_back(std::move(sv->queue.front()));
       sv->queue.pop_front();
       est = rqs[0].est_bytes;
+      // merge only when requests pile up (more waiting than slots): below that, every request
+      // gets a slot of its own and merged frames would only lengthen latencies
+      const bool backlog = sv->queue.size() >= sv->slots.size();
       const uint64_t tiles = uint64_t((rqs[0].cam.width + kTile - 1) / kTile) * uint64_t((rqs[0].cam.height + kTile - 1) / kTile);
       const uint64_t px = uint64_t(rqs[0].cam.width) * uint64_t(rqs[0].cam.height);
       uint64_t frames = rqs[0].asset.size();
       // a merged frame stays within about one 4K frame of pixels and 8192 instance frames, so that
       // its pairs and buffers stay within what one large request needs
-      for (auto it = sv->queue.begin(); it != sv->queue.end() && rqs.size() < sv->merge;) {
-        const bool fit = same_geometry(it->cam, rqs[0].cam) && sv->in_flight + est + it->est_bytes <= sv->budget &&
+      for (auto it = sv->queue.begin(); backlog && it != sv->queue.end() && rqs.size() < sv->merge;) {
+        const bool fit = same_geometry(it->cam, rqs[0].cam) && !it->heavy && !rqs[0].heavy &&
+                         sv->in_flight + est + it->est_bytes <= sv->budget &&
                          tiles * (rqs.size() + 1) <= uint64_t(kMaxTiles) && px * (rqs.size() + 1) <= kMergePixels &&
                          frames + it->asset.size() <= kMergeFrames;
         if (fit) {
@@ -977,6 +1026,8 @@ void slot_main(Server* sv, Pipe* p, size_t slot) {
         }
       }
       sv->in_flight += est;
+      for (const Request& rq : rqs) heavy |= rq.heavy;
+      if (heavy) ++sv->heavy_active;
       p->stream = sv->active == 0 ? sv->hi[slot] : sv->lo[slot];   // the previous frame of this slot has completed
       ++sv->active;
     }
@@ -1013,6 +1064,7 @@ void slot_main(Server* sv, Pipe* p, size_t slot) {
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->in_flight -= est;
       --sv->active;
+      if (heavy) --sv->heavy_active;
       if (alone) sv->alone_busy = false;
       for (const Request& rq : rqs) {
         Finished g = f;
@@ -1035,6 +1087,11 @@ void server_stop(v3dg_ctx* ctx) {
   sv->cv_work.notify_all();
   for (auto& t : sv->threads) t.join();
   for (auto& p : sv->slots) pipe_free(p.get());
+  for (cudaStream_t st : sv->hi)
+    if (st) cudaStreamSynchronize(st);
+  for (cudaStream_t st : sv->lo)
+    if (st) cudaStreamSynchronize(st);
+  if (sv->pool) cudaMemPoolDestroy(sv->pool);
   for (cudaStream_t st : sv->hi)
     if (st) cudaStreamDestroy(st);
   for (cudaStream_t st : sv->lo)
@@ -1703,22 +1760,40 @@ v3dg_status v3dg_server_start(v3dg_ctx* ctx, int slots, uint64_t hbm_budget) {
   Server* sv = new (std::nothrow) Server;
   if (!sv) return fail(c, V3DG_ENOMEM, "out of host memory");
   sv->ctx = ctx;
-  sv->budget = hbm_budget ? hbm_budget : ~uint64_t(0);
   sv->merge = size_t(ctx->serve_merge);
-  {  // each slot keeps at most its share of the budget (or of the free device memory) between requests
+  {  // no budget given: 3/4 of the device memory free now; each slot keeps at most its share of
+     // the budget between requests
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
       cudaGetLastError();
       free_b = 0;
     }
-    const uint64_t pool = hbm_budget ? hbm_budget : uint64_t(free_b) * 3 / 4;
-    if (pool) sv->slot_keep = pool / uint64_t(slots);
+    sv->budget = hbm_budget ? hbm_budget : (free_b ? uint64_t(free_b) * 3 / 4 : ~uint64_t(0));
+    // memory a slot releases returns to the shared pool and is reused without synchronising, so
+    // a slot keeps between requests only buffers within half its share of the budget
+    if (sv->budget != ~uint64_t(0)) sv->slot_keep = sv->budget / (2 * uint64_t(slots));
   }
   int least = 0, greatest = 0;
   CU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  {  // one stream-ordered pool for every slot: no device-wide synchronisation on allocation or
+     // release, and memory a slot releases is reused by the others
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    if (cudaMemPoolCreate(&sv->pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      delete sv;
+      return fail(c, V3DG_ECUDA, "cudaMemPoolCreate failed");
+    }
+    uint64_t keep = ~uint64_t(0);
+    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   for (int i = 0; i < slots; ++i) {
     auto p = std::make_unique<Pipe>();
-    p->ctx_alloc = false;   // workers use cudaMalloc: the allocator is called from the owner's thread only
+    p->ctx_alloc = false;   // workers allocate from the server's pool: the context's allocator is
+                            // called from the owner's thread only
+    p->pool = sv->pool;
     cudaStream_t hi = nullptr, lo = nullptr;
     const bool ok = cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
                     cudaStreamCreateWithPriority(&lo, cudaStreamNonBlocking, least) == cudaSuccess;
@@ -1775,7 +1850,8 @@ v3dg_status v3dg_submit(v3dg_ctx* ctx, const v3dg_request* req, uint64_t* ticket
   rq.rgb = req->rgb_out;
   rq.t = req->t_out;
   rq.out_device = req->out_on_device != 0;
-  rq.est_bytes = request_bytes(n, cam);
+  rq.est_bytes = request_bytes(n, cam, req->tau_px);
+  rq.heavy = rq.est_bytes > sv->budget / (2 * uint64_t(sv->slots.size()));
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) return V3DG_EBUSY;

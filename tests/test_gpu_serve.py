@@ -57,15 +57,17 @@ def _alone(Context, assets, reqs):
     return imgs
 
 
-@pytest.mark.parametrize("slots,budget", [(3, 0), (2, 1)])
-def test_same_alone_and_in_the_mix(api, tiny_asset, small_asset, slots, budget):
+@pytest.mark.parametrize("slots,budget,merge", [(3, 0, 1), (2, 1, 1), (3, 0, 4)])
+def test_same_alone_and_in_the_mix(api, tiny_asset, small_asset, slots, budget, merge):
     """Every request's image equals the image of the same frame rendered alone (budget 1 byte
-    admits one request at a time; budget 0 lets all slots overlap)."""
+    admits one request at a time; budget 0 lets all slots overlap; merge 4 renders waiting
+    requests of one image size together)."""
     Context, N = api
     assets = [tiny_asset, small_asset]
     reqs = _requests()
     alone = _alone(Context, assets, reqs)
     with Context(0) as ctx:
+        ctx.set_option(N.V3DG_OPT_SERVE_MERGE, merge)
         for a in assets:
             ctx.load_hierarchy(a)
         ctx.server_start(slots, budget)
