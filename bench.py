@@ -414,21 +414,26 @@ def main():
         ctx.render(rgb)
         ms, _ = ctx.stage_times(len(STAGES))
         stage_runs.append(ms)
-    # the same frames with the flat selection (the default walks large scenes top-down; same cut
-    # and image, only the select stage differs)
+    # the same frames with the flat selection and the projection in list order (the defaults walk
+    # large scenes top-down and project the render list grouped by cluster; same cut, records and
+    # image, only the select and project stages differ)
     ctx.set_option(N.V3DG_OPT_SELECT_TOPDOWN, 0)
-    flat_select = []
+    ctx.set_option(N.V3DG_OPT_PROJECT_ORDER, 0)
+    flat_select, list_project = [], []
     for fid in timed_ids:
         ctx.select(cams[fid], args.tau)
         ctx.render(rgb)
-        flat_select.append(ctx.stage_times(len(STAGES))[0][0])
+        ms, _ = ctx.stage_times(len(STAGES))
+        flat_select.append(ms[0])
+        list_project.append(ms[1])
     ctx.set_option(N.V3DG_OPT_SELECT_TOPDOWN, 2)
+    ctx.set_option(N.V3DG_OPT_PROJECT_ORDER, 2)
     ctx.set_option(N.V3DG_OPT_STAGE_TIMING, 0)
     stage_ms = {k: float(np.mean([r[i] for r in stage_runs])) for i, k in enumerate(STAGES)}
     # the blend's algorithmic work on the same frames (a separate, counting replay)
     ctx.set_option(N.V3DG_OPT_COUNT_WORK, 1)
-    frame_tot = {k: 0 for k in ("cut_nodes", "cut_gaussians", "render_nodes", "visible", "pairs", "blend_evals",
-                                "blend_contribs")}
+    frame_tot = {k: 0 for k in ("cut_nodes", "cut_gaussians", "render_nodes", "render_clusters", "visible", "pairs",
+                                "blend_evals", "blend_contribs")}
     for fid in timed_ids:
         ctx.select(cams[fid], args.tau)
         ctx.render(rgb)
@@ -517,6 +522,7 @@ def main():
             "gpu_launches": int(launches),
             "stages_ms": stage_ms,
             "select_flat_ms": float(np.mean(flat_select)),
+            "project_list_order_ms": float(np.mean(list_project)),
             "frame_mean": {k: int(round(v)) for k, v in fs.items()},
             "stages_sum_ms": float(sum(stage_ms.values())),
             "roofline": roofline,
@@ -956,12 +962,17 @@ def roofline_for(stage, stage_ms, fs, peaks, peak_kind):
     measured duration; the top-level fields are those of the dominant stage."""
     vis, pairs, nodes = fs["visible"], fs["pairs"], fs["render_nodes"]
     slots = nodes * 64
+    clusters = fs.get("render_clusters", 0)
     units = {"pair": pairs, "slot": slots}
     bytes_per = {
         # selection: the node tables are L2-resident; HBM traffic is the render list write
         "select": 8 * nodes,
-        # projection: 236 B of attributes per slot read, 48 B record + 8 B rect + 4 B key written
-        "project": 236 * slots + (48 + 8 + 4) * vis + 4 * (slots - vis),
+        # projection: 236 B of attributes per slot read -- once per distinct cluster (64 slots) when
+        # the render list is projected grouped by cluster, the instances after the first reading
+        # them from L2, plus the entry, its FP64 reference and its order (8 + 32 + 4 B per node) --
+        # and a 48 B record + 8 B rect + 4 B key written per visible Gaussian
+        "project": ((236 * 64 * clusters + 44 * nodes) if clusters else 236 * slots)
+                   + (48 + 8 + 4) * vis + 4 * (slots - vis),
         # depth sort: 4 passes of (key, value) read + write, plus the histogram read
         "depth_sort": slots * (4 * 16 + 4),
         # binning: sorted slots + pixel boxes read, pairs written

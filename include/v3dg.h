@@ -102,6 +102,10 @@ typedef struct {
   uint64_t blend_contribs;  /* of those, the ones with alpha >= 1/255 that were blended */
   uint64_t conic_fp64;      /* Gaussians whose 2D covariance had det < 1e-12 (eps2d = 0, Sec. 5.1, lets
                                it approach 0) and was formed and inverted in FP64 */
+  uint64_t render_clusters; /* distinct (asset, cluster) among the render list's entries, counted
+                               when the projection takes them grouped by cluster (see
+                               V3DG_OPT_PROJECT_ORDER) and the loaded assets hold at most 2^24
+                               nodes in all; else 0 */
 } v3dg_stats;
 
 /* Options for v3dg_set_option. */
@@ -144,6 +148,12 @@ enum {
                                 each image is the one its request gives alone, bit for bit.  Only
                                 while at least as many requests wait as there are slots.  1..64,
                                 default 1 (one request per frame). */
+  V3DG_OPT_PROJECT_ORDER = 13, /* order in which the projection takes the render list; no result
+                                depends on it: 0 list order; 1 grouped by cluster (a radix sort of
+                                the entries' cluster ids), so that the instances drawing one cluster
+                                read its attributes one after the other and share one HBM read
+                                through L2; 2 (default): grouped when the instances outnumber the
+                                assets they draw at least twice over. */
   V3DG_OPT_GRAPHS = 10         /* 1: v3dg_select only stages the camera and instances, and
                                 v3dg_render runs the selection and the whole render as one CUDA
                                 graph, captured the first time a configuration (instance and view

@@ -27,6 +27,7 @@ V3DG_OPT_BLEND_BATCH = 9
 V3DG_OPT_GRAPHS = 10
 V3DG_OPT_BLEND_MODE = 11
 V3DG_OPT_SERVE_MERGE = 12
+V3DG_OPT_PROJECT_ORDER = 13
 
 
 class V3dgError(RuntimeError):
@@ -63,7 +64,7 @@ class v3dg_stats(ctypes.Structure):
                 ("render_nodes", ctypes.c_uint64), ("visible", ctypes.c_uint64), ("pairs", ctypes.c_uint64),
                 ("overflow", ctypes.c_uint32), ("timeout", ctypes.c_uint32),
                 ("blend_evals", ctypes.c_uint64), ("blend_contribs", ctypes.c_uint64),
-                ("conic_fp64", ctypes.c_uint64)]
+                ("conic_fp64", ctypes.c_uint64), ("render_clusters", ctypes.c_uint64)]
 
 
 class v3dg_request(ctypes.Structure):

@@ -79,6 +79,7 @@ struct Pipe {
   uint32_t n_inst_frame = 0;   // instance frames of the selection: n_views * instances
   uint32_t n_views = 1;        // cameras of the current frame (same intrinsics and image size)
   int color_formats = 1;       // colour storage formats of the current instances' assets (bit 0 FP32, bit 1 FP16)
+  uint32_t distinct_assets = 0;   // assets drawn by the current instance frames
   int node_blocks = 0;
 
   DevBuf d_inst;
@@ -121,6 +122,8 @@ struct v3dg_ctx {
   int blend_batch = 512;    // records staged per blend batch: 128, 256 or 512
   int blend_mode = 0;       // 0: two-phase blend; 1: bulk-copy staging, warps composite row pairs
   int serve_merge = 1;      // server: most queued requests of one image geometry rendered together
+  int project_order = 2;    // projection by cluster: 0 never, 1 always, 2 when instances repeat assets
+  uint64_t total_nodes = 0; // nodes of all loaded assets (global cluster ids are below this)
   bool graphs = false;      // capture each frame's launches once and replay them as a CUDA graph
   Pipe main;
   Server* server = nullptr;
@@ -336,9 +339,15 @@ v3dg_status setup_views(Pipe* c, const ViewSpec* views, uint32_t n_views) {
   c->frame_asset.resize(nf);
   // the projection is specialised for the colour formats of the assets this frame draws
   c->color_formats = 0;
+  std::vector<uint8_t> drawn(c->ctx->assets.size(), 0);
   for (uint32_t v = 0; v < n_views; ++v)
-    for (uint32_t i = 0; i < views[v].n; ++i) c->color_formats |= c->ctx->assets[views[v].asset[i]].half_color ? 2 : 1;
+    for (uint32_t i = 0; i < views[v].n; ++i) {
+      c->color_formats |= c->ctx->assets[views[v].asset[i]].half_color ? 2 : 1;
+      drawn[views[v].asset[i]] = 1;
+    }
   if (!c->color_formats) c->color_formats = 1;
+  c->distinct_assets = 0;
+  for (uint8_t d : drawn) c->distinct_assets += d;
 
   // the pinned staging buffer is reused: wait until the previous upload out of it has completed
   if (c->ev_inst) CU(cudaEventSynchronize(c->ev_inst));
@@ -469,11 +478,22 @@ v3dg_status enqueue_select(Pipe* c) {
   return V3DG_OK;
 }
 
+// Whether the projection takes the render list grouped by cluster: never (option 0), always (1),
+// or (2, the default) when the frame's instance frames outnumber the assets they draw at least
+// twice over, so that clusters are drawn by several instances and their attribute reads can be
+// shared through L2.
+bool use_project_order(const Pipe* c) {
+  if (c->ctx->total_nodes > 0xFFFFFFFFull || c->ctx->project_order == 0) return false;
+  if (c->ctx->project_order == 1) return true;
+  return c->n_inst_frame >= 2 * uint64_t(std::max<uint32_t>(c->distinct_assets, 1)) && c->n_inst_frame >= 4;
+}
+
 // Start of a render: zero the render stages' counters (select's words stay, so that a render
 // list overflow still invalidates the frame) and count the slots the depth sort covers.
 __global__ void k_render_reset(uint32_t* frame, uint32_t cap_nodes) {
   const int i = threadIdx.x;
-  if (i == kVisible || i == kPairs || i == kPairsEff || i == kConicFp64 || i == kPairs64 || i == kPairs64 + 1 ||
+  if (i == kVisible || i == kPairs || i == kPairsEff || i == kConicFp64 || i == kRenderClusters || i == kPairs64 ||
+      i == kPairs64 + 1 ||
       (i > kTileCounters && i < kFrameWords))
     frame[i] = 0;
   if (i == kSlotCount) frame[kSlotCount] = min(frame[kRenderNodes], cap_nodes) * uint32_t(kSlots);
@@ -488,12 +508,35 @@ v3dg_status enqueue_render(Pipe* c, float* rgb, float* t_out) {
   stage_event(c, kStageProject);
   k_render_reset<<<1, kFrameWords, 0, c->stream>>>(frame, c->cap_nodes);
   CU(cudaGetLastError());
+  // projection order: grouped by cluster (the render list's global cluster ids, sorted on at most
+  // 24 bits, keeping the high ones) when several instances draw the same assets.  The keys and
+  // the order use d_keys1 (4 x cap_nodes words of its 4 x 64 x cap_nodes), which the depth sort
+  // only writes after the projection.
+  int key_bits = 1, key_shift = 0;
+  while ((uint64_t(1) << key_bits) < c->ctx->total_nodes) ++key_bits;
+  if (key_bits > 24) key_shift = key_bits - 24;
+  uint32_t* okeys = nullptr;
+  const uint32_t *order = nullptr, *sorted_keys = nullptr;
+  if (use_project_order(c)) okeys = P<uint32_t>(c->d_keys1);
   CU(launch_noderef(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->ctx->d_assets), k,
-                    P<float4>(c->d_ref), frame, sm, c->stream));
+                    P<float4>(c->d_ref), frame, okeys, key_shift, sm, c->stream));
+  c->ctx->launches += 2;
+  if (okeys) {
+    const size_t cn = c->cap_nodes;
+    bool oin1 = false;
+    int nl = 0;
+    CU(launch_sort(okeys, okeys + cn, okeys + 2 * cn, okeys + 3 * cn, frame + kRenderNodes, c->cap_nodes, 0,
+                   key_bits - key_shift, true, sort_scratch(c, frame + kTileCounters + 11), frame + kTimeout, c->epoch,
+                   sm, c->stream, &oin1, &nl));
+    next_epoch(c);
+    c->ctx->launches += nl;
+    order = oin1 ? okeys + 3 * cn : okeys + cn;
+    if (key_shift == 0) sorted_keys = oin1 ? okeys + 2 * cn : okeys;   // (exact cluster ids: counted)
+  }
   CU(launch_project(P<uint2>(c->d_list), c->cap_nodes, P<InstFrame>(c->d_inst), P<AssetDev>(c->ctx->d_assets), k,
                     P<float4>(c->d_ref), P<float4>(c->d_rec), P<uint2>(c->d_rect), P<uint32_t>(c->d_keys0), frame,
-                    c->color_formats, sm, c->stream));
-  c->ctx->launches += 3;
+                    order, sorted_keys, c->color_formats, sm, c->stream));
+  c->ctx->launches += 1;
 
   stage_event(c, kStageDepthSort);
   bool in1 = false;
@@ -599,7 +642,8 @@ std::vector<uint64_t> graph_key(Pipe* c, float* rgb, float* t_out) {
   const v3dg_ctx* ctx = c->ctx;
   std::vector<uint64_t> k = {c->n_inst_frame, c->n_views, uint64_t(c->node_blocks), c->cap_nodes, c->cap_pairs,
                              c->cap_slots, c->status_words, uint64_t(uintptr_t(rgb)), uint64_t(uintptr_t(t_out)),
-                             uint64_t(use_topdown(c)), uint64_t(ctx->blend_batch), uint64_t(ctx->blend_mode),
+                             uint64_t(use_topdown(c)), uint64_t(use_project_order(c)), uint64_t(ctx->blend_batch),
+                             uint64_t(ctx->blend_mode),
                              ctx->split_pairs,
                              uint64_t(ctx->count_work), uint64_t(c->color_formats), ctx->assets.size(),
                              uint64_t(uintptr_t(ctx->d_assets.p))};
@@ -1187,6 +1231,10 @@ v3dg_status v3dg_set_option(v3dg_ctx* ctx, int option, int64_t value) {
       if (value < 1 || value > 64) return fail(c, V3DG_EINVAL, "requests per launch must be in [1, 64]");
       ctx->serve_merge = int(value);
       break;
+    case V3DG_OPT_PROJECT_ORDER:
+      if (value < 0 || value > 2) return fail(c, V3DG_EINVAL, "projection order must be 0, 1 or 2");
+      ctx->project_order = int(value);
+      break;
     case V3DG_OPT_BLEND_MODE:
       if (value != 0 && value != 1) return fail(c, V3DG_EINVAL, "blend mode must be 0 or 1");
       ctx->blend_mode = int(value);
@@ -1344,9 +1392,12 @@ v3dg_status v3dg_load_hierarchy(v3dg_ctx* ctx, const v3dg_hierarchy_desc* d, uin
   }
   ctx->assets.push_back(std::move(a));
   std::vector<AssetDev> table(ctx->assets.size());
+  ctx->total_nodes = 0;
   for (size_t i = 0; i < ctx->assets.size(); ++i) {
     const AssetHost& h = ctx->assets[i];
     AssetDev& t = table[i];
+    t.node_base = uint32_t(ctx->total_nodes);   // (not used once the total passes 2^32)
+    ctx->total_nodes += h.n_nodes;
     t.own = P<float4>(h.own);
     t.par = P<float4>(h.par);
     t.bound = P<float4>(h.bound);
@@ -1460,6 +1511,7 @@ v3dg_status v3dg_frame_stats(v3dg_ctx* ctx, v3dg_stats* out) {
   out->visible = f[kVisible];
   out->pairs = f[kPairs];
   out->conic_fp64 = f[kConicFp64];
+  out->render_clusters = f[kRenderClusters];
   uint32_t sticky[2] = {0, 0};
   CU(cudaMemcpy(sticky, P<uint32_t>(c->d_misc) + 12, sizeof sticky, cudaMemcpyDeviceToHost));
   CU(cudaMemset(P<uint32_t>(c->d_misc) + 12, 0, sizeof sticky));

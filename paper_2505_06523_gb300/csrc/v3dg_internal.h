@@ -43,7 +43,7 @@ struct AssetDev {
   const float4* sub_bound;
   const float* sub_sigma;
   uint32_t root;
-  uint32_t pad;
+  uint32_t node_base;      // global id of node 0: the node counts of the assets loaded before this one
 };
 
 // Per (frame, instance) constants, computed on the host in FP64 (128-byte aligned, 256 B).
@@ -79,6 +79,7 @@ enum Counter : int {
   kPairsEff = 8,           // pairs the tile sort / blend use: kPairs, or 0 when the frame overflowed
   kTdReached = 9,          // top-down selection: (instance, node) entries it tested
   kConicFp64 = 10,         // Gaussians whose 2D covariance had det < 1e-12 and was inverted in FP64
+  kRenderClusters = 11,    // distinct clusters of the render list (projection grouped by cluster)
   kPairs64 = 12,           // [12, 14): the pair total as a 64-bit sum (detects totals beyond 2^32)
   kNumCounters = 16,
   kTileCounters = 16,      // [16, 48): atomic tile counters of the chained-scan kernels
@@ -127,9 +128,12 @@ cudaError_t launch_select_topdown(const InstFrame* inst, int n_inst, const Asset
 //   [0] = (U0 hi, U0 lo, V0 hi, V0 lo): pixel position of the node's mean centre as float pairs
 //   [1] = (rho_x, rho_y, Pz, mode): X/Z, Y/Z and Z of that centre in view space; mode 1 =
 //         compensated (centre well in front), 0 = direct (rho_x, rho_y then hold X, Y).
+// order_keys (may be NULL): also writes, per entry, its cluster's global id (node_base + node)
+// shifted right by key_shift, the key that groups the render list by cluster for the projection.
 cudaError_t launch_noderef(const uint2* render_list, uint32_t cap_nodes, const InstFrame* inst,
                            const AssetDev* assets, const CamConst& cam, float4* ref,
-                           const uint32_t* frame, int sm_count, cudaStream_t st);
+                           const uint32_t* frame, uint32_t* order_keys, int key_shift, int sm_count,
+                           cudaStream_t st);
 
 // Records (3 float4 per slot, slot = render index * 64 + j):
 //   [0] = (u_rel, v_rel, na, nb), [1] = (nc, log2 o, r, g), [2] = (b, tile origin, x range, y range)
@@ -138,10 +142,15 @@ cudaError_t launch_noderef(const uint2* render_list, uint32_t cap_nodes, const I
 // ranges x0 | x1 << 16, y0 | y1 << 16 of the alpha >= 1/255 ellipse's bounding box.
 // color_formats: bit 0 set if some loaded asset stores its colour planes in float32, bit 1 if
 // some asset stores them in float16 (the kernel is specialised for the formats present).
+// order (may be NULL: list order): a permutation of the render-list indices that the warps take
+// in turn.  Each entry's outputs stay at its own slots, so the order changes no result; ordered by
+// cluster, the instances that draw one cluster read its attributes one after the other, and all
+// but the first find them in L2.  sorted_keys (may be NULL): the global cluster id of each
+// position of `order`; the distinct ones are counted into frame[kRenderClusters].
 cudaError_t launch_project(const uint2* render_list, uint32_t cap_nodes, const InstFrame* inst,
                            const AssetDev* assets, const CamConst& cam, const float4* ref, float4* rec,
-                           uint2* rect, uint32_t* keys, uint32_t* frame, int color_formats, int sm_count,
-                           cudaStream_t st);
+                           uint2* rect, uint32_t* keys, uint32_t* frame, const uint32_t* order,
+                           const uint32_t* sorted_keys, int color_formats, int sm_count, cudaStream_t st);
 
 // Radix sort of (key, value) pairs, n read from *n_dev (clamped to cap).  Ping-pongs between
 // (k0, v0) and (k1, v1); the result lands in (k0, v0) when the pass count is even, else in

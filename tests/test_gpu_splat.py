@@ -196,6 +196,47 @@ def test_quadrant_split_is_bit_identical(Context, tiny_asset, small_asset):
     assert (whole["rgb"] == split["rgb"]).all() and (whole["T"] == split["T"]).all()
 
 
+@pytest.mark.parametrize("scene", ["crowd", "single"])
+def test_projection_order_changes_nothing(Context, tiny_asset, small_asset, scene):
+    """Projecting the render list grouped by cluster (V3DG_OPT_PROJECT_ORDER 1) or in list order (0)
+    gives the same records, pairs, counters and image, bit for bit; the default (2) picks the
+    grouping for the crowd (200 instances of 2 assets) and list order for one instance."""
+    from paper_2505_06523_gb300._native import V3DG_OPT_PROJECT_ORDER
+    if scene == "crowd":
+        inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+        cam = scenes.crowd_camera(40, 640, 360)
+    else:
+        inst = scenes.single_instance()
+        cam = scenes.tiny_camera()
+    outs = [_frame(Context, [tiny_asset, small_asset], inst, cam, 1.0, {V3DG_OPT_PROJECT_ORDER: o}) for o in (0, 1, 2)]
+    ref = outs[0]
+    assert float(np.abs(ref["rgb"]).sum()) > 0
+    for o in outs[1:]:
+        assert (o["rgb"] == ref["rgb"]).all() and (o["T"] == ref["T"]).all()
+        for k in ref["proj"]:
+            assert np.array_equal(o["proj"][k], ref["proj"][k], equal_nan=True), k
+        for k in ref["pairs"]:
+            assert np.array_equal(o["pairs"][k], ref["pairs"][k]), k
+        assert {k: v for k, v in o["stats"].items() if k != "render_clusters"} == \
+            {k: v for k, v in ref["stats"].items() if k != "render_clusters"}
+    # the distinct clusters of the render list, counted only by the grouped projection
+    cut = outs[0]["cut"]
+    cut_clusters = np.unique(inst.asset[cut[:, 0]].astype(np.uint64) << np.uint64(32) | cut[:, 1].astype(np.uint64))
+    assert ref["stats"]["render_clusters"] == 0
+    assert 0 < outs[1]["stats"]["render_clusters"] <= min(ref["stats"]["render_nodes"], len(cut_clusters))
+    assert outs[2]["stats"]["render_clusters"] == (outs[1]["stats"]["render_clusters"] if scene == "crowd" else 0)
+
+
+def test_projection_order_option_range(Context):
+    from paper_2505_06523_gb300._native import V3DG_OPT_PROJECT_ORDER
+    with Context(0) as ctx:
+        for v in (0, 1, 2):
+            ctx.set_option(V3DG_OPT_PROJECT_ORDER, v)
+        for v in (-1, 3):
+            with pytest.raises(Exception):
+                ctx.set_option(V3DG_OPT_PROJECT_ORDER, v)
+
+
 def _fp16_rounded(asset):
     import copy
     a = copy.copy(asset)
