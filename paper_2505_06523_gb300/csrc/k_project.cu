@@ -128,7 +128,6 @@ __device__ __forceinline__ bool project_one(const GaussPre& G, uint32_t j, size_
                                             const CamConst& cam, const float4 bc, int nsh, const TC* __restrict__ col,
                                             float4* __restrict__ rec, uint2* __restrict__ rect,
                                             uint32_t* __restrict__ keys, uint32_t* __restrict__ frame) {
-  constexpr size_t st = kSlots;
   const float4 M0 = E.m0, M1 = E.m1, M2 = E.m2, CA = E.cam, r0 = E.r0, r1 = E.r1;
   const struct { float m[12]; float cam_a[3]; } I = {{M0.x, M0.y, M0.z, M0.w, M1.x, M1.y, M1.z, M1.w, M2.x, M2.y, M2.z, M2.w},
                                                     {CA.x, CA.y, CA.z}};
