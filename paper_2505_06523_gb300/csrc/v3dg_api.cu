@@ -21,6 +21,7 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <set>
 #include <unordered_set>
 #include <vector>
 
@@ -901,7 +902,9 @@ struct Finished {
 // requests that arrive while others run start at once and their kernels overlap on the GPU.  A
 // request that starts while no other one is on the GPU runs on its slot's high-priority stream,
 // the others on the low-priority one: a frame that has the GPU keeps it (its latency stays that of
-// a frame alone), and the frames admitted beside it fill the SMs it leaves idle.
+// a frame alone), and the frames admitted beside it fill the SMs it leaves idle.  A request whose
+// estimate is at most a quarter of every running one's also takes the high-priority stream, so a
+// small frame does not wait behind a large one.
 struct Server {
   v3dg_ctx* ctx = nullptr;
   uint64_t budget = 0;
@@ -917,6 +920,7 @@ struct Server {
   std::unordered_map<uint64_t, Finished> finished;
   std::unordered_set<uint64_t> pending;   // issued and not yet reported by v3dg_poll
   uint64_t next_ticket = 1, in_flight = 0, active = 0, waiting_alone = 0, heavy_active = 0;
+  std::multiset<uint64_t> active_est;   // memory estimates (a proxy of the work) of the frames on the GPU
   bool alone_busy = false;   // a slot renders requests alone after running out of device memory
   bool stop = false;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
@@ -1072,8 +1076,12 @@ void slot_main(Server* sv, Pipe* p, size_t slot) {
       sv->in_flight += est;
       for (const Request& rq : rqs) heavy |= rq.heavy;
       if (heavy) ++sv->heavy_active;
-      p->stream = sv->active == 0 ? sv->hi[slot] : sv->lo[slot];   // the previous frame of this slot has completed
+      // high priority for a frame that starts alone, or that is far smaller than every frame on
+      // the GPU (it then shares the SMs with them instead of queueing behind them)
+      const bool small = !sv->active_est.empty() && est * 4 <= *sv->active_est.begin();
+      p->stream = sv->active == 0 || small ? sv->hi[slot] : sv->lo[slot];   // (this slot's previous frame has completed)
       ++sv->active;
+      sv->active_est.insert(est);
     }
     Finished f;
     bool alone = false;
@@ -1108,6 +1116,7 @@ void slot_main(Server* sv, Pipe* p, size_t slot) {
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->in_flight -= est;
       --sv->active;
+      sv->active_est.erase(sv->active_est.find(est));
       if (heavy) --sv->heavy_active;
       if (alone) sv->alone_busy = false;
       for (const Request& rq : rqs) {
