@@ -15,6 +15,8 @@
 //   are one contiguous block of planes of 64 values, so every warp load is one 128-byte line).
 //   Writes a 48-byte blend record, the pixel box and the float32 depth key per Gaussian;
 //   culled slots get the key 0xFFFFFFFF so that the depth sort moves them behind all visible ones.
+#include <algorithm>
+
 #include <cuda_fp16.h>
 
 #include "dev_common.cuh"
@@ -293,6 +295,7 @@ __device__ __forceinline__ uint32_t project_run(int lane, int a, int b, uint32_t
 constexpr int kMaxChunk = 32;
 // chunk sizes (measured on the crowd: 8 to 32 within 1% grouped; 16 best in list order)
 constexpr int kProjChunkGrouped = 32, kProjChunkList = 16;
+constexpr int kProjChunkCounter = 15;   // the frame's tile-counter word of the chunk queue
 template <int kFormats>
 __global__ void __launch_bounds__(kProjThreads, 2)
 k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* __restrict__ inst,
@@ -305,10 +308,13 @@ k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* _
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t n_nodes = min(frame[kRenderNodes], cap_nodes);
   const uint32_t n_chunks = (n_nodes + chunk - 1) / chunk;
-  const uint32_t nwarps = (gridDim.x * kProjThreads) >> 5;
   EntryConst* ent = s_ent[warp];
   uint32_t nvis = 0, ndist = 0;
-  for (uint32_t ch = (blockIdx.x * kProjThreads + threadIdx.x) >> 5; ch < n_chunks; ch += nwarps) {
+  for (;;) {   // persistent warps take the chunks in turn from a frame counter
+    uint32_t ch = 0;
+    if (lane == 0) ch = atomicAdd(frame + kTileCounters + kProjChunkCounter, 1u);
+    ch = __shfl_sync(0xffffffffu, ch, 0);
+    if (ch >= n_chunks) break;
     const uint32_t p = ch * chunk + lane;
     const bool okp = lane < chunk && p < n_nodes;
     uint32_t ci = 0, node = 0, asset = 0xFFFFFFFFu;
@@ -377,6 +383,20 @@ k_project(const uint2* __restrict__ list, uint32_t cap_nodes, const InstFrame* _
 
 }  // namespace
 
+int g_project_blocks_per_sm[4] = {2, 2, 2, 2};   // resident k_project blocks per SM, per colour-format set
+
+cudaError_t project_set_attributes() {
+  int n1 = 0, n2 = 0, n3 = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_project<1>, kProjThreads, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_project<2>, kProjThreads, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_project<3>, kProjThreads, 0);
+  if (e != cudaSuccess) return e;
+  g_project_blocks_per_sm[1] = n1;
+  g_project_blocks_per_sm[2] = n2;
+  g_project_blocks_per_sm[3] = n3;
+  return cudaSuccess;
+}
+
 cudaError_t launch_noderef(const uint2* list, uint32_t cap, const InstFrame* inst, const AssetDev* assets,
                            const CamConst& cam, float4* ref, const uint32_t* frame, uint32_t* order_keys,
                            int key_shift, int sm_count, cudaStream_t st) {
@@ -388,7 +408,9 @@ cudaError_t launch_project(const uint2* list, uint32_t cap_nodes, const InstFram
                            const CamConst& cam, const float4* ref, float4* rec, uint2* rect, uint32_t* keys,
                            uint32_t* frame, const uint32_t* order, const uint32_t* sorted_keys,
                            int color_formats, int sm_count, cudaStream_t st) {
-  const int grid = sm_count * 8;
+  // persistent grid: the resident blocks of the specialisation
+  const int f = color_formats == 2 ? 2 : color_formats == 3 ? 3 : 1;
+  const int grid = sm_count * std::max(g_project_blocks_per_sm[f], 1);
   const int chunk = order ? kProjChunkGrouped : kProjChunkList;
   if (color_formats == 2)
     k_project<2><<<grid, kProjThreads, 0, st>>>(list, cap_nodes, inst, assets, cam, ref, rec, rect, keys, frame, order, sorted_keys, chunk);

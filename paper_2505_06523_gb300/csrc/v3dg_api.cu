@@ -1178,7 +1178,8 @@ v3dg_status v3dg_create(int device, const v3dg_allocator* alloc, v3dg_ctx** out)
   }
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-      sort_set_attributes() != cudaSuccess || blend_set_attributes() != cudaSuccess) {
+      sort_set_attributes() != cudaSuccess || blend_set_attributes() != cudaSuccess ||
+      project_set_attributes() != cudaSuccess) {
     delete ctx;
     return V3DG_ECUDA;
   }

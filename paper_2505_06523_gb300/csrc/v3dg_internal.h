@@ -178,6 +178,7 @@ constexpr int kMaxTiles = 1 << 20;
 // (so that no attribute call happens during a stream capture).
 cudaError_t sort_set_attributes();
 cudaError_t blend_set_attributes();
+cudaError_t project_set_attributes();
 
 // Expansion of the depth-sorted visible Gaussians into (tile, slot) pairs in depth order; writes
 // frame[kPairs] (the total) and frame[kPairsEff] (0 if the frame overflowed).  rect: per slot,
