@@ -3,10 +3,10 @@
 // One histogram kernel reads the keys once and counts all digit passes; then each 8-bit pass is
 // a single kernel: a block takes the next 4096-key tile (virtual id from an atomic counter),
 // ranks its keys per digit within each warp (stable: item-major then lane order within a warp,
-// warps in order), publishes its per-digit counts, reorders the tile by digit in shared
-// memory (so that the global writes come out in runs), and looks back across earlier tiles per
-// digit (one thread per digit, 4 status words per round, bounded waits) to find its global
-// offsets.
+// warps in order), publishes its per-digit counts (the sums of the warps' counts), reorders the
+// tile by digit in shared memory (so that the global writes come out in runs), and looks back
+// across earlier tiles per digit (one thread per digit, 4 status words per round, bounded waits)
+// to find its global offsets.
 #include <algorithm>
 
 #include "dev_common.cuh"
@@ -136,7 +136,6 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   const uint32_t tile = s_tile;
   if (tile >= ntiles) return;
   for (int i = tid; i < kWarps * kBins / 2; i += kSortThreads) reinterpret_cast<uint32_t*>(&s_wh[0][0])[i] = 0;
-  if (tid < kBins) s_cnt[tid] = 0;
   __syncthreads();
   const uint32_t base = tile * kSortTile + warp * (kSortItems * 32);
 
@@ -148,13 +147,6 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     key[i] = ok ? kin[idx] : 0xFFFFFFFFu;
     val[i] = kImplicit ? idx : (ok ? vin[idx] : 0u);
   }
-  // the tile's digit counts first, published at once, so that later tiles' look-backs find them
-  // while this tile is still ranking
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i)
-    if (base + i * 32 + lane < n) atomicAdd(&s_cnt[(key[i] >> shift) & dmask], 1u);
-  __syncthreads();
-  if (tid <= dmask) chain_publish(status + tid, kBins, tile, s_cnt[tid], epoch);   // digits of the pass only
   // warp-level stable ranking: item-major, then lane order.  The lanes that share a digit come
   // from a shared-memory OR of lane bits (measured faster than match.any), or are the whole warp
   // when every lane has the same digit (common in the high digits of the depth keys, where the
@@ -196,6 +188,10 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
       s_wh[w][tid] = uint16_t(cnt);
       cnt += c;
     }
+  }
+  if (tid <= dmask) {   // the tile's digit counts, published as soon as they are known
+    chain_publish(status + tid, kBins, tile, cnt, epoch);
+    s_cnt[tid] = cnt;
   }
   uint32_t total;
   const uint32_t start = block_exclusive_scan<kWarps>(cnt, s_scan, &total);
