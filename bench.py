@@ -952,7 +952,7 @@ BLEND_OPS_EVAL, BLEND_OPS_CONTRIB = 8, 10
 # of its frame.  Scaled to a full launch by the units processed (traffic grows with them).
 NCU_DRAM_PER_UNIT = {
     "blend": (7.21, "pair", "profiles/k_blend_crowd_small.md"),      # (250.3 + 6.2) MB / 35.6M pairs
-    "project": (220.0, "slot", "profiles/k_project_crowd_small.md"),  # (2,999.5 + 854.7) MB / 17.5M slots
+    "project": (98.9, "slot", "profiles/k_project_crowd_small.md"),   # (897.0 + 838.8) MB / 17.56M slots
     "bin": (11.84, "pair", "profiles/k_expand_crowd_small.md"),       # (175.4 + 245.8) MB / 35.6M pairs
 }
 
