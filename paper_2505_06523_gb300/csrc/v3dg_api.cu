@@ -1045,6 +1045,11 @@ void slot_main(Server* sv, Pipe* p, size_t slot) {
         const Request& next = sv->queue.front();
         if (sv->active == 0) return true;
         if (next.heavy && sv->heavy_active) return false;   // large frames saturate the GPU on their own
+        // beside frames on the GPU, start another only under a backlog (two or more waiting):
+        // the stages run on persistent grids that hold every SM until they finish, so frames
+        // that share the GPU take turns kernel by kernel, and a frame started beside others
+        // finishes later than it would queued, unless requests pile up
+        if (sv->queue.size() < 2) return false;
         return sv->in_flight + next.est_bytes <= sv->budget;
       });
       if (sv->queue.empty()) return;   // stopping and nothing left
