@@ -306,18 +306,21 @@ v3dg_status v3dg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, uint64_t n, 
  * repeats its per-frame path (select, Sec. 3.4, then splat, Sec. 2.1) once per request.
  *
  * v3dg_server_start starts `slots` workers (1..64) on the context's device.  Each worker owns its
- * own streams and frame buffers (from cudaMalloc: the context's allocator is only ever called from
- * the thread that owns the context) and shares the loaded assets (load them all first).  Requests
- * wait in arrival order; a free worker takes the next one when the device-memory estimates of the
- * requests in flight plus its own fit `hbm_budget` bytes (0: 3/4 of the device memory free at
- * start; a request is always admitted when none is in flight), so requests overlap on the GPU as
- * soon as they arrive.  A request's estimate (also used to size its frame buffers before its
+ * own streams and frame buffers (from the server's stream-ordered memory pool: the context's
+ * allocator is only ever called from the thread that owns the context) and shares the loaded
+ * assets (load them all first).  Requests wait in arrival order; a free worker takes the next one
+ * at once when none is in flight, and beside others while two or more requests wait and the
+ * device-memory estimates of the requests in flight plus its own fit `hbm_budget` bytes (0: 3/4 of
+ * the device memory free at start), so frames overlap on the GPU when requests pile up (a frame
+ * started beside others would otherwise only take turns with them kernel by kernel: every stage
+ * runs on a persistent grid).  A request's estimate (also used to size its frame buffers before its
  * first frame) grows with its instances, the square root of 1 / tau_px and, for its pairs, of its
  * pixel count (about 9 MB per instance of a 1M-leaf crowd at 1920x1080, tau 1).  A request
  * estimated above half its slot's share of the budget is heavy: it saturates the GPU on its own,
  * so at most one heavy request is in flight (light ones still overlap it).  A
- * request that starts while no other one is in flight runs on a high-priority stream, the others
- * on low-priority streams, so a frame alone keeps its solo latency and later ones fill idle SMs.
+ * request that starts while no other one is in flight, or whose estimate is at most a quarter of
+ * every running one's, runs on a high-priority stream, the others on low-priority streams, so a
+ * frame alone keeps its solo latency and later ones fill idle SMs.
  * Each frame is checked and re-run with larger buffers on overflow, as v3dg_render does with
  * V3DG_OPT_SYNC_CHECK.  Device memory: the slots allocate from one stream-ordered pool of the
  * server; a slot that holds more frame buffers than half its share of the budget releases them
