@@ -227,6 +227,34 @@ def test_projection_order_changes_nothing(Context, tiny_asset, small_asset, scen
     assert outs[2]["stats"]["render_clusters"] == (outs[1]["stats"]["render_clusters"] if scene == "crowd" else 0)
 
 
+def test_projection_order_mixed_formats(Context, tiny_asset, small_asset):
+    """Grouped projection over assets of both colour formats (one float32, one float16): the
+    mixed-format kernel gives the same image in both orders, and it matches the oracle on the
+    float16-rounded attributes."""
+    from paper_2505_06523_gb300._native import V3DG_OPT_ATTR_FP16, V3DG_OPT_PROJECT_ORDER
+    inst = scenes.crowd_instances(200, n_assets=2, half_extent=70.0)
+    cam = scenes.crowd_camera(40, 640, 360)
+    outs = []
+    for o in (0, 1):
+        with Context(0) as ctx:
+            ctx.set_option(V3DG_OPT_PROJECT_ORDER, o)
+            ctx.load_hierarchy(tiny_asset)
+            ctx.set_option(V3DG_OPT_ATTR_FP16, 1)
+            ctx.load_hierarchy(small_asset)
+            ctx.set_instances(inst)
+            ctx.select(cam, 1.0)
+            rgb, T = ctx.render(want_T=True)
+            outs.append((rgb.cpu().numpy(), T.cpu().numpy(), ctx.get_projected(), ctx.frame_stats()))
+    (rgb0, T0, p0, st0), (rgb1, T1, p1, st1) = outs
+    assert float(np.abs(rgb0).sum()) > 0
+    assert (rgb0 == rgb1).all() and (T0 == T1).all()
+    for k in p0:
+        assert np.array_equal(p0[k], p1[k], equal_nan=True), k
+    assert st0["render_clusters"] == 0 and st1["render_clusters"] > 0
+    assets = [tiny_asset, _fp16_rounded(small_asset)]
+    assert_image_matches_oracle(rgb1, T1, assets, inst, cam, 1.0)
+
+
 def test_projection_order_option_range(Context):
     from paper_2505_06523_gb300._native import V3DG_OPT_PROJECT_ORDER
     with Context(0) as ctx:
