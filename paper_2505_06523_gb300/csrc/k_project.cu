@@ -122,12 +122,10 @@ struct EntryConst {
 static_assert(offsetof(InstFrame, m) % 16 == 0 && offsetof(InstFrame, cam_a) % 16 == 0 &&
               offsetof(InstFrame, s) == offsetof(InstFrame, cam_a) + 12, "InstFrame float4 views");
 
-// Projects Gaussian j of a cluster (pre-computed values G, colour planes col) for one entry (its
-// constants E) into slot `slot`; returns whether it is visible.  bc: the cluster's bound centre
-// (asset frame).
-template <typename TC>
-__device__ __forceinline__ bool project_one(const GaussPre& G, uint32_t j, size_t slot, const EntryConst& E,
-                                            const CamConst& cam, const float4 bc, int nsh, const TC* __restrict__ col,
+// Projects a Gaussian of a cluster (its pre-computed values G) for one entry (its constants E)
+// into slot `slot`; returns whether it is visible.  bc: the cluster's bound centre (asset frame).
+__device__ __forceinline__ bool project_one(const GaussPre& G, size_t slot, const EntryConst& E,
+                                            const CamConst& cam, const float4 bc, int nsh,
                                             float4* __restrict__ rec, uint2* __restrict__ rect,
                                             uint32_t* __restrict__ keys, uint32_t* __restrict__ frame) {
   const float4 M0 = E.m0, M1 = E.m1, M2 = E.m2, CA = E.cam, r0 = E.r0, r1 = E.r1;
@@ -282,7 +280,7 @@ __device__ __forceinline__ uint32_t project_run(int lane, int a, int b, uint32_t
         keys[slot] = 0xFFFFFFFFu;
         continue;
       }
-      nvis += project_one<TC>(G, j, slot, ent[e], cam, bc, nsh, col, rec, rect, keys, frame) ? 1u : 0u;
+      nvis += project_one(G, slot, ent[e], cam, bc, nsh, rec, rect, keys, frame) ? 1u : 0u;
     }
   }
   return nvis;
