@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--assets", type=int, default=N_ASSETS, help="fewer assets: a smaller case for profiling")
     ap.add_argument("--instances", type=int, default=N_INST, help="fewer instances: a smaller case for profiling")
     ap.add_argument("--slots", type=int, default=4, help="server slots of the served leg (0: no served leg)")
-    ap.add_argument("--serve-requests", type=int, default=150)
+    ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--views", type=int, default=16, help="views per launch of the batched leg (0: none)")
     ap.add_argument("--no-extra-legs", action="store_true", help="skip the orbit table and the no-LOD comparison")
     ap.add_argument("--mix-seconds", type=float, default=2.5,
