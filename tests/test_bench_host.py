@@ -42,6 +42,21 @@ def test_hbm_stage_fields():
     assert r["traffic"] == pytest.approx(per * 20 * 64)
 
 
+def test_project_bytes_grouped_by_cluster():
+    """With the render list projected grouped by cluster (render_clusters counted), the projection
+    reads each distinct cluster's 64 x 236 B once plus 44 B per entry (entry, FP64 reference,
+    order); the writes are unchanged."""
+    fs = dict(FS, render_clusters=5.0)
+    r = bench.roofline_for("project", STAGE_MS, fs, PEAKS, "measured")
+    slots, vis = 20 * 64, 1000
+    want = 236 * 64 * 5 + 44 * 20 + (48 + 8 + 4) * vis + 4 * (slots - vis)
+    assert r["achieved"] == pytest.approx(want / 1e-3 / 1e9, rel=1e-12)
+    # the other stages do not depend on the grouping
+    r0 = bench.roofline_for("project", STAGE_MS, FS, PEAKS, "measured")
+    for k in ("depth_sort", "bin", "tile_sort", "ranges", "blend"):
+        assert r["per_stage"][k] == r0["per_stage"][k], k
+
+
 def test_every_stage_and_the_frame():
     r = bench.roofline_for("project", STAGE_MS, FS, PEAKS, "measured")
     ps = r["per_stage"]
