@@ -669,7 +669,8 @@ def serve_mix_leg(ctx, scenes_fp32, scenes_fp16, slots, tuned, seconds, max_outs
     (100 / 1000 / 5000 instances, 720p / 1080p / 4K, tau 0.5-4 px, a walk frame), images back into
     pinned host memory.  served: `slots` slots, FP16 colour, autotuned blend; served_merged: the
     same, and up to 8 waiting requests of one image size rendered as one frame while requests pile
-    up; plain: one slot, FP32 attributes, one request per frame, default blend (serial plain
+    up; served_one_slot: FP16 colour and the autotuned blend on one slot (no frames side by side);
+    plain: one slot, FP32 attributes, one request per frame, default blend (serial plain
     rendering of the same stream).  A client keeps at most
     max_outstanding requests in flight (host output buffers) and drops arrivals beyond that
     (counted).  Latency = submit -> done on the server's clock."""
@@ -684,7 +685,7 @@ def serve_mix_leg(ctx, scenes_fp32, scenes_fp16, slots, tuned, seconds, max_outs
 
     out = {"seconds_per_rate": seconds, "max_outstanding": max_outstanding, "slots": slots, "rates": []}
     arms = {"plain": (1, 1, scenes_fp32, DEFAULT_BLEND), "served": (slots, 1, scenes_fp16, tuned),
-            "served_merged": (slots, 8, scenes_fp16, tuned)}
+            "served_merged": (slots, 8, scenes_fp16, tuned), "served_one_slot": (1, 1, scenes_fp16, tuned)}
     rng = np.random.default_rng(3000)
     for rate in rates:
         n = max(min_requests, int(round(rate * seconds)))   # arrivals at this rate (at least min_requests)
