@@ -33,6 +33,37 @@ def test_binding_covers_the_header(native):
     assert set(_declared()) == set(native.SIGNATURES)
 
 
+def _header_enum(prefix):
+    """name -> value of the header's enumerators that start with `prefix` (explicit values, or the
+    previous value + 1)."""
+    text = open(os.path.join(ROOT, "include", "v3dg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body in re.findall(r"enum\s*(?:\w+\s*)?\{(.*?)\}", text, flags=re.S):
+        value = -1
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            m = re.match(r"(\w+)\s*(?:=\s*(-?\w+))?$", item)
+            assert m, item
+            value = int(m.group(2), 0) if m.group(2) else value + 1
+            if m.group(1).startswith(prefix):
+                out[m.group(1)] = value
+    return out
+
+
+def test_option_and_status_constants_match_the_header(native):
+    """Every option and status value of the header has a binding constant with the same value."""
+    for prefix in ("V3DG_OPT_", "V3DG_OK", "V3DG_E"):
+        want = _header_enum(prefix)
+        assert want, prefix
+        for name, value in want.items():
+            assert getattr(native, name) == value, name
+    status = {**_header_enum("V3DG_OK"), **_header_enum("V3DG_E")}
+    assert native.STATUS_NAMES == [n for n, _ in sorted(status.items(), key=lambda kv: kv[1])]
+
+
 def test_struct_sizes_match_the_header(native, tmp_path):
     """The ctypes structures have the sizes and field offsets that a C compiler gives the header's
     structures (compiled here with the host C compiler)."""
