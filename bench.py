@@ -652,7 +652,7 @@ def mix_scenes(inst1000, n_assets):
     return {100: scenes.subset(inst1000, np.arange(100)), 1000: inst1000, 5000: five}
 
 
-def mix_requests(n, seed, n_assets_offset=0, inst_sets=None):
+def mix_requests(n, seed):
     """n requests drawn from config 5's mix: scene size, resolution, tau and walk frame."""
     rng = np.random.default_rng(seed)
     out = []

@@ -105,3 +105,27 @@ def test_clock_record_summary():
     s = c.summary()
     assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and math.isclose(s["sm_mhz"], 1500.0)
     assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_request_mix_draws_the_configured_classes():
+    """Config 5's request mix: every draw is one of 100 / 1000 / 5000 instances, 720p / 1080p / 4K,
+    tau 0.5 / 1 / 2 / 4 and a walk frame; the draws are seeded, and 2,000 of them reach every
+    combination of scene size and resolution."""
+    a = bench.mix_requests(2000, seed=7)
+    assert a == bench.mix_requests(2000, seed=7) and a != bench.mix_requests(2000, seed=8)
+    sizes, res, taus, frames = zip(*a)
+    assert set(sizes) == {100, 1000, 5000}
+    assert set(res) == {(1280, 720), (1920, 1080), (3840, 2160)}
+    assert set(taus) == {0.5, 1.0, 2.0, 4.0}
+    assert min(frames) >= 0 and max(frames) < 300
+    assert len({(n, r) for n, r, _, _ in a}) == 9
+
+
+def test_request_mix_scenes():
+    """The mix's scenes: the first 100 crowd instances, the crowd, and the crowd extended to 5000."""
+    from synth import scenes
+    crowd = scenes.crowd_instances(1000, n_assets=3)
+    sc = bench.mix_scenes(crowd, 3)
+    assert {k: v.n for k, v in sc.items()} == {100: 100, 1000: 1000, 5000: 5000}
+    assert (sc[100].trans == crowd.trans[:100]).all() and (sc[5000].trans[:1000] == crowd.trans).all()
+    assert sc[5000].asset.max() < 3
