@@ -1,7 +1,8 @@
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs, onesweep style.
 //
-// One histogram kernel reads the keys once and counts all digit passes; then each 8-bit pass is
-// a single kernel: a block takes the next 4096-key tile (virtual id from an atomic counter),
+// One histogram kernel reads the keys once and counts all digit passes (as many passes as 8-bit
+// digits need, the key's bits then spread evenly over them: 13 tile bits as 7 + 6); then each
+// pass is a single kernel: a block takes the next 4096-key tile (virtual id from an atomic counter),
 // ranks its keys per digit within each warp (stable: item-major then lane order within a warp,
 // warps in order), publishes its per-digit counts (the sums of the warps' counts), reorders the
 // tile by digit in shared memory (so that the global writes come out in runs), and looks back
@@ -28,7 +29,7 @@ constexpr int kHistRun = 16;
 
 __global__ void __launch_bounds__(256)
 k_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev, uint32_t cap, int begin_bit,
-       int end_bit, int passes, uint32_t* __restrict__ hist) {
+       int end_bit, int passes, int width, uint32_t* __restrict__ hist) {
   __shared__ uint32_t sh[4][kBins];
   for (int i = threadIdx.x; i < 4 * kBins; i += blockDim.x) sh[i / kBins][i % kBins] = 0;
   __syncthreads();
@@ -37,8 +38,8 @@ k_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev, ui
   uint32_t m[4];
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    sh_[p] = begin_bit + 8 * p;
-    m[p] = end_bit - sh_[p] >= 8 ? 0xFFu : ((1u << max(end_bit - sh_[p], 0)) - 1u);
+    sh_[p] = begin_bit + width * p;
+    m[p] = (1u << min(max(end_bit - sh_[p], 0), width)) - 1u;
   }
   const uint32_t runs = (n + kHistRun - 1) / kHistRun;
   const bool aligned = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
@@ -266,6 +267,7 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
                         uint32_t* err_flag, uint32_t& epoch, int sm_count, cudaStream_t st, bool* result_in_1,
                         int* launches) {
   const int passes = (end_bit - begin_bit + 7) / 8;
+  const int width = passes > 0 ? (end_bit - begin_bit + passes - 1) / passes : 8;   // balanced digits
   *result_in_1 = false;
   if (passes <= 0 || cap == 0) return cudaSuccess;
   if (passes > 4) return cudaErrorInvalidValue;
@@ -275,13 +277,13 @@ cudaError_t launch_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, 
   const uint32_t grid = std::min<uint32_t>(max_tiles, uint32_t(sm_count) * uint32_t(g_sort_blocks_per_sm));
   cudaError_t e = cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * kBins * passes, st);
   if (e != cudaSuccess) return e;
-  k_hist<<<sm_count * 4, 256, 0, st>>>(k0, n_dev, cap, begin_bit, end_bit, passes, sc.hist);
+  k_hist<<<sm_count * 4, 256, 0, st>>>(k0, n_dev, cap, begin_bit, end_bit, passes, width, sc.hist);
   k_hist_scan<<<1, kBins, 0, st>>>(sc.hist, passes, sc.hist + 4 * kBins);
   *launches += 2;
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int p = 0; p < passes; ++p) {
-    const int shift = begin_bit + 8 * p;
-    const uint32_t dmask = end_bit - shift >= 8 ? 0xFFu : ((1u << (end_bit - shift)) - 1u);
+    const int shift = begin_bit + width * p;
+    const uint32_t dmask = (1u << std::min(end_bit - shift, width)) - 1u;
     epoch = (epoch + 1) & 0x3FFFFFFFu;
     if (epoch == 0) epoch = 1;
     const uint32_t ep = epoch;
