@@ -985,6 +985,10 @@ def roofline_for(stage, stage_ms, fs, peaks, peak_kind):
     hbm_peak = float(peaks["hbm_gbs"])
     per_stage = {k: {"bound": "hbm", "gbs": v / (stage_ms[k] / 1000.0) / 1e9, "frac": v / (stage_ms[k] / 1000.0) / 1e9 / hbm_peak,
                      "ms": stage_ms[k]} for k, v in bytes_per.items() if stage_ms.get(k)}
+    if "select" in per_stage:   # its node tables stay in L2 / L1: the HBM figures are its writes only
+        per_stage["select"]["bound"] = "latency"
+        per_stage["select"]["note"] = ("node tables L2/L1-resident; HBM bytes are the render list written; "
+                                       "issue and L2 figures in profiles/k_select_crowd_small.md")
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = FP32_LANES * mhz * 1e6 / 1e12
     if fs.get("blend_evals") and stage_ms.get("blend"):

@@ -42,6 +42,12 @@ def test_hbm_stage_fields():
     assert r["traffic"] == pytest.approx(per * 20 * 64)
 
 
+def test_select_is_labelled_by_its_own_bound():
+    r = bench.roofline_for("project", STAGE_MS, FS, PEAKS, "measured")
+    assert r["per_stage"]["select"]["bound"] == "latency" and "profiles/" in r["per_stage"]["select"]["note"]
+    assert all(r["per_stage"][k]["bound"] == "hbm" for k in ("project", "depth_sort", "bin", "tile_sort", "ranges"))
+
+
 def test_project_bytes_grouped_by_cluster():
     """With the render list projected grouped by cluster (render_clusters counted), the projection
     reads each distinct cluster's 64 x 236 B once plus 44 B per entry (entry, FP64 reference,
